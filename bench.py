@@ -1,0 +1,396 @@
+"""Throughput benchmark of the fused D2Q9 KBC stream-collide step.
+
+Workload (default): KBC D2Q9, model B, FP32 deviation storage, 16384^2 doubly
+periodic grid (A-B population buffers of 19.3 GB, far larger than the 129 MB
+L2), seeded random turbulent initial field (E(k) ~ k^4 exp(-2 (k/16)^2),
+u_rms = 0.03, Re = 1e5).  One step = one pull-stream + collide update of
+every node.  Metric: million lattice-node updates per second (MLUPS).
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+on the host cores instead, on a bounded sample of the same workload.
+Multi-GPU runs (torchrun, one rank per GPU) are independent replicas: each
+rank advances its own grid, with no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS and % of HBM roofline (FP64/FP32/FP16-store) at stated error vs FP64 oracle"
+UNIT = "MLUPS"
+WORKLOAD = ("KBC D2Q9 throughput stress: 16384^2 doubly periodic, seeded random turbulent "
+            "initial field (E(k)~k^4 exp(-2(k/16)^2), u_rms=0.03, Re=1e5)")
+DTYPE_BYTES = {"f64": 8, "f32": 4, "f16": 2}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=1000)
+    p.add_argument("--warmup", type=int, default=10)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n", type=int, default=16384)
+    p.add_argument("--dtype", default="f32", choices=["f64", "f32", "f16"])
+    p.add_argument("--variant", default="B", choices=["lbgk", "A", "B", "C", "D"])
+    p.add_argument("--extras", type=int, default=1, help="also time f64/f16/LBGK (0: skip)")
+    p.add_argument("--extra-steps", type=int, default=100)
+    p.add_argument("--e2e", type=int, default=1)
+    p.add_argument("--cpu-baseline", type=int, default=1)
+    p.add_argument("--seed", type=int, default=2024)
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------- helpers
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1507_02509_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_from_profile(dtype: str, n: int):
+    """DRAM bytes per launch of the step kernel from the committed ncu
+    summary, scaled to n^2 nodes; None if missing or taken on other sources."""
+    path = os.path.join(ROOT, "profiles", f"kbc_step_rows_{dtype}_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    with open(path) as f:
+        for line in f:
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                vals[k.strip()] = v.strip()
+    try:
+        if vals.get("kernel_source_hash") != kernel_source_hash():
+            return None
+        return float(vals["dram_bytes_per_node"]) * n * n
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def reynolds_viscosity(n: int, urms: float = 0.03, re: float = 1e5):
+    from paper_1507_02509_gb300 import viscosity_for_reynolds
+
+    return viscosity_for_reynolds(n, 0.5 * urms * urms, re)
+
+
+# ---------------------------------------------------------------- CPU oracle
+
+def cpu_oracle_rate(steps: int, n: int = 1024, seed: int = 2024, max_seconds: float = 20.0):
+    """MLUPS of the FP64 oracle on all host cores on an n^2 field of the same
+    workload family; runs at most `steps` steps or about max_seconds."""
+    import oracle
+    from paper_1507_02509_gb300 import beta_from_viscosity, flows
+
+    cores = os.cpu_count() or 1
+    nu = reynolds_viscosity(n)
+    beta = beta_from_viscosity(nu)
+    rho, ux, uy = flows.turbulence(n, k0=16, urms=0.03, seed=seed)
+    g = oracle.init_feq(rho, ux, uy)
+    # one probe step to size the run
+    t0 = time.perf_counter()
+    g = oracle.step(g, oracle.B, beta, 1, nthreads=cores)
+    per = time.perf_counter() - t0
+    k = max(1, min(steps, int(max_seconds / max(per, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.step(g, oracle.B, beta, k, nthreads=cores)
+    dt = time.perf_counter() - t0
+    return n * n * k / dt / 1e6, cores, k, n
+
+
+# ---------------------------------------------------------------- GPU arm
+
+def time_steps(lat, steps, stream):
+    import torch
+
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    lat.step(steps)
+    end.record(stream)
+    end.synchronize()
+    lat.sync()
+    return start.elapsed_time(end) / 1e3
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1507_02509_gb300 import Lattice, beta_from_viscosity, capi, flows
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    capi.load()
+
+    n = args.n
+    nu = reynolds_viscosity(n)
+    beta = beta_from_viscosity(nu)
+    rho, ux, uy = flows.turbulence(n, k0=16, urms=0.03, seed=args.seed + rank,
+                                   backend="torch", device=f"cuda:{local}")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # ---- headline: default workload
+    lat = Lattice(n, n, variant=args.variant, beta=beta, dtype=args.dtype)
+    lat.init(rho, ux, uy)
+    lat.step(args.warmup)
+    lat.sync()
+    guard_nodes = lat.guard_count() if args.dtype != "f64" and args.variant != "lbgk" else 0
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t = time_steps(lat, args.steps, stream)
+    barrier()
+    torch.cuda.synchronize()
+    t = max_over_ranks(t)
+    guard_on = args.dtype != "f64" and args.variant != "lbgk"
+    launches_per_step = 2 if guard_on else 1
+    value = world * n * n * args.steps / t / 1e6
+
+    # ---- roofline: the step kernel alone (guard pass off), same launch shape
+    bpu = DTYPE_BYTES[args.dtype] * 18
+    k_roof = min(args.steps, 200)
+    if guard_on:
+        lat.set_guard(0.0)
+    t_roof = time_steps(lat, k_roof, stream)
+    if guard_on:
+        lat.set_guard(1e-15)
+    kernel_s = t_roof / k_roof
+    peak, peak_kind = load_peaks()
+    achieved = bpu * n * n / kernel_s / 1e9
+    traffic = traffic_from_profile(args.dtype, n)
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "algorithmic_bytes": bpu * n * n, "peak_kind": peak_kind,
+                "kernel": f"step_rows<{args.variant},{args.dtype}>",
+                "kernel_ms": round(kernel_s * 1e3, 4)}
+
+    # ---- e2e through the C ABI with pinned host buffers
+    e2e = None
+    if args.e2e:
+        h_rho = torch.empty((n, n), dtype=torch.float64, pin_memory=True)
+        h_u = torch.empty((2, n, n), dtype=torch.float64, pin_memory=True)
+        h_rho.copy_(rho)
+        h_u[0].copy_(ux)
+        h_u[1].copy_(uy)
+        o_rho = torch.empty((n, n), dtype=torch.float64, pin_memory=True)
+        o_u = torch.empty((2, n, n), dtype=torch.float64, pin_memory=True)
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        capi.kbc_init(lat.h, h_rho, h_u)
+        capi.kbc_step(lat.h, args.steps)
+        capi.kbc_moments(lat.h, o_rho, o_u)
+        lat.sync()
+        te = max_over_ranks(time.perf_counter() - t0)
+        barrier()
+        hb = h_rho.numel() * 8 + h_u.numel() * 8
+        db = o_rho.numel() * 8 + o_u.numel() * 8
+        e2e = {"value": round(world * n * n * args.steps / te / 1e6, 1), "unit": UNIT,
+               "h2d_bytes_per_step": hb // args.steps, "d2h_bytes_per_step": db // args.steps,
+               "what": ("kbc_init from pinned host rho,u + kbc_step(K) + kbc_moments to pinned "
+                        "host; copies amortised over the K steps")}
+        del h_rho, h_u, o_rho, o_u
+    lat.close()
+    del lat
+    torch.cuda.empty_cache()
+
+    # ---- extras: other storage / LBGK on the same field
+    extras = {}
+    if args.extras:
+        for tag, dt, var in (("f64", "f64", args.variant), ("f16", "f16", args.variant),
+                             ("lbgk_f32", "f32", "lbgk"), ("lbgk_f64", "f64", "lbgk"),
+                             ("A_f32", "f32", "A"), ("C_f32", "f32", "C"), ("D_f32", "f32", "D")):
+            if dt == args.dtype and var == args.variant:
+                continue
+            lx = Lattice(n, n, variant=var, beta=beta, dtype=dt)
+            lx.init(rho, ux, uy)
+            lx.step(3)
+            lx.sync()
+            te = time_steps(lx, args.extra_steps, stream)
+            g_on = dt != "f64" and var != "lbgk" and dt == "f32"
+            if g_on:
+                lx.set_guard(0.0)
+                tk = time_steps(lx, args.extra_steps, stream) / args.extra_steps
+            else:
+                tk = te / args.extra_steps
+            b = DTYPE_BYTES[dt] * 18
+            extras[tag] = {"mlups": round(n * n * args.extra_steps / te / 1e6, 1),
+                           "kernel_gbs": round(b * n * n / tk / 1e9, 1),
+                           "frac": round(b * n * n / tk / 1e9 / peak, 4),
+                           "steps": args.extra_steps}
+            lx.close()
+            del lx
+            torch.cuda.empty_cache()
+
+    cpu = None
+    if args.cpu_baseline and rank == 0:
+        rate, cores, k, nc = cpu_oracle_rate(args.steps)
+        cpu = {"value": round(rate, 3), "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"FP64 C oracle, {nc}^2 field of the same generator, KBC B, {k} steps"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(t / args.steps * 1e3, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": n, "variant": args.variant,
+                       "storage": args.dtype, "beta": beta, "nu": nu,
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "l2": "inputs larger than L2 (A-B buffers "
+                             f"{2 * 9 * n * n * DTYPE_BYTES[args.dtype] / 1e9:.1f} GB vs 129 MB)",
+                       "guard_nodes_last_step": guard_nodes},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": args.steps * launches_per_step,
+            "clocks": clk.summary(), "extras": extras,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    """The oracle on the host cores: each step is one oracle step of a
+    1024^2 periodic field of the same workload family."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    from paper_1507_02509_gb300 import beta_from_viscosity, flows
+
+    n = 1024
+    cores = os.cpu_count() or 1
+    beta = beta_from_viscosity(reynolds_viscosity(n))
+    rho, ux, uy = flows.turbulence(n, k0=16, urms=0.03, seed=args.seed)
+    g = oracle.init_feq(rho, ux, uy)
+    g = oracle.step(g, oracle.B, beta, args.warmup, nthreads=cores)
+    t0 = time.perf_counter()
+    oracle.step(g, oracle.B, beta, args.steps, nthreads=cores)
+    dt = time.perf_counter() - t0
+    v = n * n * args.steps / dt / 1e6
+    line = {
+        "metric": METRIC, "value": round(v, 3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "impl": "reference",
+        "config": {"workload": WORKLOAD, "n": args.n, "variant": "B", "storage": "f64",
+                   "sample": f"{n}^2 periodic field of the same generator per step"},
+        "cpu_baseline": {"value": round(v, 3), "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"FP64 C oracle, {n}^2 field, {args.steps} steps"},
+        "e2e": {"value": round(v, 3), "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

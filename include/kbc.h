@@ -1,0 +1,183 @@
+/*
+ * kbc.h -- C ABI of the GB300 (sm_103a) D2Q9 KBC lattice Boltzmann library.
+ *
+ * The library advances a doubly periodic nx x ny D2Q9 population field with
+ * the fused pull-stream + collide update of Eq. Egeneral (Sec. 1), where the
+ * post-collision state uses the one-parameter KBC mirror state of
+ * Eq. ksh-mirror (Sec. 2) with the moment grouping of Table 1 (variants A-D)
+ * and the entropic stabiliser gamma* of Eq. result21 (Sec. 4), or the plain
+ * LBGK mirror of Eq. LBGKmirr.  Reference: Bosch, Chikatamarla, Karlin,
+ * "Entropic multi-relaxation models for simulation of fluid turbulence".
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Status.   Every call returns a kbc_status (0 = KBC_OK, negative = error)
+ *           and never aborts, traps or exits.  kbc_last_error(h) gives a
+ *           human-readable message for the last failing call on h.
+ * Layout.   Scalar fields are [ny][nx] row-major, x fastest.  Velocity
+ *           fields are [2][ny][nx] (u_x plane, then u_y plane).  Population
+ *           fields are [9][ny][nx] with population index i = 3(b+1) + (a+1)
+ *           for the lattice velocity v_i = (a, b), a, b in {-1, 0, 1}.
+ *           All external fields are IEEE double.
+ * Pointers. Field pointers may be host memory (pageable or pinned) or device
+ *           memory of the handle's device; the library tells them apart
+ *           with cudaPointerGetAttributes and stages host data through a
+ *           device buffer.  Caller memory is borrowed only for the duration
+ *           of the call.
+ * Ordering. All device work is issued on the stream bound with
+ *           kbc_set_stream (default: the legacy default stream).  Calls
+ *           that return device results into device memory are asynchronous
+ *           on that stream; calls that return host results (host
+ *           pointers, kbc_diagnostics, kbc_adjoint's scalars) synchronise
+ *           that stream only, with a bounded wait (KBC_ERR_TIMEOUT).
+ * State.    After kbc_init and n steps the handle holds the post-collision
+ *           field f'(., n) of Eq. Egeneral.  rho and u are the same for the
+ *           pre- and post-collision fields because the collision conserves
+ *           them (Eq. k_conservation, Eq. sh_conservation).
+ * Memory.   The handle owns its device buffers (two population fields, the
+ *           A-B pair, plus small scratch), obtained from the allocator set
+ *           with kbc_set_allocator at kbc_create time (default cudaMalloc).
+ */
+#ifndef KBC_GB300_H
+#define KBC_GB300_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct kbc_ctx* kbc_handle;
+
+/* Collision model: LBGK (Eq. LBGKmirr) or the KBC variants of Table 1.
+ * A: s = {Pi~, N~, T~}, B: s = {Pi~, N~} (central moments, Sec. 2, Eq. cm);
+ * C: s = {Pi, N, T},   D: s = {Pi, N}   (natural moments, Eq. natmoments1). */
+enum kbc_variant { KBC_LBGK = 0, KBC_A = 1, KBC_B = 2, KBC_C = 3, KBC_D = 4 };
+
+/* Storage of the population field in device memory.
+ * KBC_F64:     f_i - W_i in IEEE double, arithmetic in double.
+ * KBC_F32_DEV: f_i - W_i in float, arithmetic in float (moment sums and gamma
+ *              in float, with an FP64 re-evaluation of nodes whose
+ *              <dh|dh> falls below the guard, see kbc_set_guard).
+ * KBC_F16_DEV: (f_i - W_i) / W_i * S in IEEE half with a per-run scale S
+ *              (kbc_set_f16_scale), arithmetic in float. */
+enum kbc_dtype { KBC_F64 = 0, KBC_F32_DEV = 1, KBC_F16_DEV = 2 };
+
+/* gamma of Eq. result21 (entropic), or a fixed value (2 reproduces LBGK,
+ * 1/beta the regularised limit discussed after Eq. dsdh1B). */
+enum kbc_gamma_mode { KBC_GAMMA_ENTROPIC = 0, KBC_GAMMA_FIXED = 1 };
+
+enum kbc_status {
+    KBC_OK = 0,
+    KBC_ERR_ARG = -1,       /* invalid argument or size                       */
+    KBC_ERR_CUDA = -2,      /* a CUDA runtime call failed                     */
+    KBC_ERR_NOMEM = -3,     /* the allocator returned NULL                    */
+    KBC_ERR_NONFINITE = -4, /* the field holds NaN or Inf (the update blew up) */
+    KBC_ERR_TIMEOUT = -5,   /* a bounded wait on the stream ran out           */
+    KBC_ERR_STATE = -6      /* call out of order (e.g. step before init)      */
+};
+
+/* Number of doubles written by kbc_diagnostics. */
+#define KBC_DIAG_N 10
+
+/* Device allocator hook: returns a device pointer of at least `bytes` bytes
+ * (256-byte aligned) or NULL; `stream` is the handle's bound stream. */
+typedef void* (*kbc_alloc_fn)(size_t bytes, void* stream, void* user);
+typedef void (*kbc_free_fn)(void* ptr, void* stream, void* user);
+
+/* Set the process-wide allocator used by subsequent kbc_create calls
+ * (NULL, NULL restores cudaMalloc/cudaFree).  A handle frees its buffers
+ * with the allocator it was created with. */
+int kbc_set_allocator(kbc_alloc_fn alloc, kbc_free_fn release, void* user);
+
+/* Create a handle for an nx x ny doubly periodic grid on the current CUDA
+ * device.  beta is the relaxation parameter of Eq. Egeneral, related to the
+ * kinematic viscosity by nu = cs^2 (1/(2 beta) - 1/2), cs^2 = 1/3
+ * (Eq. viscosity).  Requirements: nx, ny >= 1, nx * ny <= 2^31 - 1,
+ * 0 < beta <= 1, variant and dtype from their enums; else KBC_ERR_ARG.
+ * Grids with nx a multiple of the vector row width (128 for F32, 64 for F64,
+ * 256 for F16) take the vectorised row kernel, all others a per-node kernel
+ * with the same arithmetic.  *out is NULL on failure. */
+int kbc_create(int nx, int ny, int variant, double beta, int dtype, kbc_handle* out);
+
+/* Free the handle's device buffers (after synchronising its stream). */
+int kbc_destroy(kbc_handle h);
+
+/* Bind a cudaStream_t (passed as void*); NULL = legacy default stream. */
+int kbc_set_stream(kbc_handle h, void* cuda_stream);
+
+/* gamma mode (enum kbc_gamma_mode) and the fixed gamma it uses.  Ignored by
+ * KBC_LBGK, whose mirror state has no gamma. */
+int kbc_set_gamma_mode(kbc_handle h, int mode, double gamma_fixed);
+
+/* Threshold on <dh|dh> (entropic scalar product of Sec. 4, computed with the
+ * weights rho/f^eq_i) below which an F32/F16 node is recomputed entirely in
+ * FP64 from its stored populations by a second pass.  0 disables the pass.
+ * Defaults: 1e-15 for F32 (about 30x the float rounding level of that sum
+ * for |u| ~ 0.03), 0 for F16; F64 ignores it. */
+int kbc_set_guard(kbc_handle h, double threshold);
+
+/* Number of nodes the FP64 guard pass re-evaluated in the most recent step
+ * (synchronises the stream; 0 when the pass is off). */
+int kbc_guard_count(kbc_handle h, long long* count);
+
+/* Scale S of the F16 encoding (f - W)/W * S; must be set before kbc_init.
+ * Default 1. */
+int kbc_set_f16_scale(kbc_handle h, double scale);
+
+/* Initialise the field to the equilibrium f^eq(rho, u) of Eq. Eq at every
+ * node.  rho: [ny][nx], u: [2][ny][nx]; host or device. */
+int kbc_init(kbc_handle h, const double* rho, const double* u);
+
+/* Initialise with Grad's approximation (Eq. Grad) using the pressure tensor
+ * Pi^eq + Pi^(1) of Eq. Peq and Eq. P1AC, velocity gradients by periodic
+ * central differences of u. */
+int kbc_init_grad(kbc_handle h, const double* rho, const double* u);
+
+/* Overwrite / read the population field f[9][ny][nx] (FP64).  set rounds to
+ * the handle's storage; get returns the stored values exactly. */
+int kbc_set_populations(kbc_handle h, const double* f);
+int kbc_get_populations(kbc_handle h, double* f);
+
+/* Advance nsteps >= 0 time steps of Eq. Egeneral (pull f_i(x) = f'_i(x - v_i)
+ * with periodic wrap, then collide).  Asynchronous: returns after enqueueing.
+ * Returns KBC_ERR_NONFINITE if a NaN/Inf was detected by an earlier step of
+ * this handle whose result has reached the host (the detection is copied
+ * back asynchronously after each call; kbc_sync makes it current). */
+int kbc_step(kbc_handle h, int nsteps);
+
+/* Wait (bounded by timeout_s seconds; <= 0 means 600) for the handle's
+ * stream; returns KBC_ERR_NONFINITE if any step so far produced NaN/Inf. */
+int kbc_sync(kbc_handle h, double timeout_s);
+
+/* Populations of selected nodes: f[k][9] (FP64) for node indices
+ * nodes[k] = y * nx + x, k < count.  nodes and f may be host or device
+ * memory; indices outside [0, nx*ny) give KBC_ERR_ARG (checked on the device,
+ * reported after the call synchronises). */
+int kbc_probe(kbc_handle h, int count, const long long* nodes, double* f);
+
+/* rho [ny][nx] and u [2][ny][nx] of the current field (FP64). */
+int kbc_moments(kbc_handle h, double* rho, double* u);
+
+/* Global diagnostics (FP64 device reductions), out[KBC_DIAG_N] on the host:
+ *   [0] sum rho  [1] sum rho u_x  [2] sum rho u_y
+ *   [3] E = mean |u|^2/2   [4] Z = mean w^2/2, w = d_x u_y - d_y u_x by
+ *       periodic central differences
+ *   [5] mean, [6] min, [7] max of gamma of the collision the next step
+ *       performs (2 for LBGK)
+ *   [8] spatial std of |u|^2/2   [9] spatial std of w^2/2 */
+int kbc_diagnostics(kbc_handle h, double* out);
+
+/* Bytes of population traffic per lattice-node update of this handle's
+ * storage (9 reads + 9 writes), for roofline accounting. */
+int kbc_bytes_per_update(kbc_handle h, double* bytes);
+
+/* Message describing the last error on h (or of the last kbc_create when h
+ * is NULL).  Valid until the next call on h. */
+const char* kbc_last_error(kbc_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KBC_GB300_H */

@@ -1,0 +1,651 @@
+// C ABI of the D2Q9 KBC library (declarations and contracts: include/kbc.h).
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <thread>
+
+#include "../../include/kbc.h"
+#include "kbc_launch.cuh"
+
+namespace kbc {
+
+__global__ void diag_final(const double* __restrict__ part, int nblocks, double* __restrict__ out,
+                           long long total)
+{
+    // one block; thread t sums blocks t, t + blockDim, ... in a fixed order
+    __shared__ double sm[kDiagParts][kDiagBlock];
+    double acc[kDiagParts] = {0, 0, 0, 0, 0, 0, 0, 0, 1e300, -1e300};
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc[k] += part[(long long)b * kDiagParts + k];
+        acc[8] = fmin(acc[8], part[(long long)b * kDiagParts + 8]);
+        acc[9] = fmax(acc[9], part[(long long)b * kDiagParts + 9]);
+    }
+#pragma unroll
+    for (int k = 0; k < kDiagParts; ++k) sm[k][threadIdx.x] = acc[k];
+    __syncthreads();
+    for (int s = kDiagBlock / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) sm[k][threadIdx.x] += sm[k][threadIdx.x + s];
+            sm[8][threadIdx.x] = fmin(sm[8][threadIdx.x], sm[8][threadIdx.x + s]);
+            sm[9][threadIdx.x] = fmax(sm[9][threadIdx.x], sm[9][threadIdx.x + s]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double inv = 1.0 / (double)total;
+        const double e = sm[3][0] * inv, z = sm[5][0] * inv;
+        out[0] = sm[0][0];
+        out[1] = sm[1][0];
+        out[2] = sm[2][0];
+        out[3] = e;
+        out[4] = z;
+        out[5] = sm[7][0] * inv;
+        out[6] = sm[8][0];
+        out[7] = sm[9][0];
+        out[8] = sqrt(fmax(sm[4][0] * inv - e * e, 0.0));
+        out[9] = sqrt(fmax(sm[6][0] * inv - z * z, 0.0));
+    }
+}
+
+}  // namespace kbc
+
+using namespace kbc;
+
+namespace {
+
+struct Allocator {
+    kbc_alloc_fn alloc = nullptr;
+    kbc_free_fn release = nullptr;
+    void* user = nullptr;
+};
+
+std::mutex g_alloc_mu;
+Allocator g_alloc;
+std::string g_create_error;
+
+}  // namespace
+
+struct kbc_ctx {
+    int nx = 0, ny = 0, variant = 0, dtype = 0, device = 0, num_sms = 1;
+    double beta = 1.0;
+    int gamma_mode = KBC_GAMMA_ENTROPIC;
+    double gamma_fixed = 2.0;
+    double guard = 0.0;
+    float f16_scale = 1.0f;
+    long long plane = 0;  // elements per population plane
+    size_t elem = 8;      // bytes per stored element
+    void* buf[2] = {nullptr, nullptr};
+    int cur = 0;          // buffer holding the current state
+    int* fix = nullptr;   // [0..1] counters, [64..] list of node indices
+    int fix_slot = 0;
+    int* flag_dev = nullptr;
+    int* flag_host = nullptr;  // pinned
+    double* diag_part = nullptr;
+    int diag_nblocks = 0;
+    double* diag_out = nullptr;  // device, KBC_DIAG_N doubles
+    void* stage = nullptr;       // device staging for host pointers
+    size_t stage_bytes = 0;
+    bool initialized = false;
+    cudaStream_t stream = nullptr;
+    Allocator al;
+    std::string err;
+};
+
+namespace {
+
+int fail(kbc_ctx* h, int code, const std::string& msg)
+{
+    if (h) h->err = msg;
+    else g_create_error = msg;
+    return code;
+}
+
+int cuda_fail(kbc_ctx* h, cudaError_t e, const char* where)
+{
+    return fail(h, KBC_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+void* dev_alloc(kbc_ctx* h, size_t bytes)
+{
+    if (bytes == 0) bytes = 256;
+    if (h->al.alloc) return h->al.alloc(bytes, (void*)h->stream, h->al.user);
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void dev_free(kbc_ctx* h, void* p)
+{
+    if (!p) return;
+    if (h->al.release) h->al.release(p, (void*)h->stream, h->al.user);
+    else cudaFree(p);
+}
+
+bool is_device_ptr(const void* p)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+size_t elem_size(int dtype) { return dtype == KBC_F64 ? 8 : dtype == KBC_F32_DEV ? 4 : 2; }
+int vec_width(int dtype) { return dtype == KBC_F64 ? 2 : dtype == KBC_F32_DEV ? 4 : 8; }
+
+StepArgs args_of(const kbc_ctx* h)
+{
+    StepArgs a;
+    a.nx = h->nx;
+    a.ny = h->ny;
+    a.plane = h->plane;
+    a.cs.scale = h->f16_scale;
+    a.cs.inv_scale = 1.0f / h->f16_scale;
+    a.beta = h->beta;
+    a.fixed = (h->gamma_mode == KBC_GAMMA_FIXED) ? 1 : 0;
+    a.gamma_fixed = h->gamma_fixed;
+    a.guard = (h->dtype == KBC_F64) ? 0.0 : h->guard;
+    a.fix_count = h->fix;
+    a.fix_list = h->fix ? h->fix + 64 : nullptr;
+    a.fix_slot = h->fix_slot;
+    a.flag = h->flag_dev;
+    return a;
+}
+
+// Stage `bytes` from a host or device pointer into device memory.
+int stage_in(kbc_ctx* h, const void* src, size_t bytes, const void** dev)
+{
+    if (is_device_ptr(src)) {
+        *dev = src;
+        return KBC_OK;
+    }
+    if (h->stage_bytes < bytes) {
+        dev_free(h, h->stage);
+        h->stage = dev_alloc(h, bytes);
+        h->stage_bytes = h->stage ? bytes : 0;
+        if (!h->stage) return fail(h, KBC_ERR_NOMEM, "staging allocation failed");
+    }
+    cudaError_t e = cudaMemcpyAsync(h->stage, src, bytes, cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "host-to-device copy");
+    *dev = h->stage;
+    return KBC_OK;
+}
+
+int wait_stream(kbc_ctx* h, double timeout_s)
+{
+    if (timeout_s <= 0) timeout_s = 600.0;
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t e = cudaStreamQuery(h->stream);
+        if (e == cudaSuccess) break;
+        if (e != cudaErrorNotReady) return cuda_fail(h, e, "stream");
+        const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (el > timeout_s) return fail(h, KBC_ERR_TIMEOUT, "timed out waiting for the stream");
+        std::this_thread::sleep_for(std::chrono::microseconds(el < 0.01 ? 5 : 200));
+    }
+    return KBC_OK;
+}
+
+template <class F>
+cudaError_t by_codec(int dtype, F&& fn)
+{
+    switch (dtype) {
+    case KBC_F64: return fn(CodecF64{});
+    case KBC_F32_DEV: return fn(CodecF32{});
+    case KBC_F16_DEV: return fn(CodecF16{});
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+int check_h(kbc_ctx* h)
+{
+    if (!h) return KBC_ERR_ARG;
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+    return KBC_OK;
+}
+
+}  // namespace
+
+static int init_common(kbc_handle h, const double* rho, const double* u, bool grad)
+{
+    int rc = check_h(h);
+    if (rc) return rc;
+    if (!rho || !u) return fail(h, KBC_ERR_ARG, "NULL field");
+    const size_t n = (size_t)h->nx * h->ny;
+    const double *drho, *du;
+
+    // stage both fields through one buffer when they are on the host
+    const bool hr = !is_device_ptr(rho), hu = !is_device_ptr(u);
+    if (hr || hu) {
+        const size_t need = 3 * n * sizeof(double);
+        if (h->stage_bytes < need) {
+            dev_free(h, h->stage);
+            h->stage = dev_alloc(h, need);
+            h->stage_bytes = h->stage ? need : 0;
+            if (!h->stage) return fail(h, KBC_ERR_NOMEM, "staging allocation failed");
+        }
+        double* st = static_cast<double*>(h->stage);
+        cudaError_t e = cudaMemcpyAsync(st, rho, n * sizeof(double), cudaMemcpyDefault, h->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(st + n, u, 2 * n * sizeof(double), cudaMemcpyDefault, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "field upload");
+        drho = st;
+        du = st + n;
+    } else {
+        drho = rho;
+        du = u;
+    }
+
+    StepArgs a = args_of(h);
+    cudaError_t e = by_codec(h->dtype, [&](auto c) {
+        using C = decltype(c);
+        return launch_init<C>(drho, du, du + n, h->buf[h->cur], a, grad, h->stream, h->num_sms);
+    });
+    if (e != cudaSuccess) return cuda_fail(h, e, "init launch");
+    h->initialized = true;
+    return KBC_OK;
+}
+
+// Run `kernel(dst_device)` writing `bytes` of output, into `out` (host or device).
+template <class K>
+static int produce(kbc_handle h, void* out, size_t bytes, K&& kernel)
+{
+    const bool dev = is_device_ptr(out);
+    void* target = out;
+    if (!dev) {
+        if (h->stage_bytes < bytes) {
+            dev_free(h, h->stage);
+            h->stage = dev_alloc(h, bytes);
+            h->stage_bytes = h->stage ? bytes : 0;
+            if (!h->stage) return fail(h, KBC_ERR_NOMEM, "staging allocation failed");
+        }
+        target = h->stage;
+    }
+    cudaError_t e = kernel(target);
+    if (e != cudaSuccess) return cuda_fail(h, e, "launch");
+    if (!dev) {
+        e = cudaMemcpyAsync(out, target, bytes, cudaMemcpyDeviceToHost, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "device-to-host copy");
+        return wait_stream(h, 0);
+    }
+    return KBC_OK;
+}
+
+extern "C" {
+
+int kbc_set_allocator(kbc_alloc_fn alloc, kbc_free_fn release, void* user)
+{
+    if ((alloc == nullptr) != (release == nullptr)) return KBC_ERR_ARG;
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    g_alloc.alloc = alloc;
+    g_alloc.release = release;
+    g_alloc.user = user;
+    return KBC_OK;
+}
+
+int kbc_create(int nx, int ny, int variant, double beta, int dtype, kbc_handle* out)
+{
+    if (!out) return fail(nullptr, KBC_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (nx < 1 || ny < 1 || (long long)nx * ny > 2147483647LL)
+        return fail(nullptr, KBC_ERR_ARG, "grid size out of range");
+    if (!(beta > 0.0 && beta <= 1.0)) return fail(nullptr, KBC_ERR_ARG, "beta must lie in (0, 1]");
+    if (variant < KBC_LBGK || variant > KBC_D) return fail(nullptr, KBC_ERR_ARG, "bad variant");
+    if (dtype < KBC_F64 || dtype > KBC_F16_DEV) return fail(nullptr, KBC_ERR_ARG, "bad dtype");
+    kbc_ctx* h = new (std::nothrow) kbc_ctx;
+    if (!h) return fail(nullptr, KBC_ERR_NOMEM, "host allocation failed");
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        h->al = g_alloc;
+    }
+    h->nx = nx;
+    h->ny = ny;
+    h->variant = variant;
+    h->beta = beta;
+    h->dtype = dtype;
+    h->elem = elem_size(dtype);
+    h->guard = (dtype == KBC_F32_DEV) ? 1e-15 : 0.0;
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        std::string m = std::string("no CUDA device: ") + cudaGetErrorString(e);
+        delete h;
+        return fail(nullptr, KBC_ERR_CUDA, m);
+    }
+    const long long per = 256 / (long long)h->elem;
+    h->plane = (((long long)nx * ny + per - 1) / per) * per;
+    const size_t field = (size_t)9 * h->plane * h->elem;
+    h->buf[0] = dev_alloc(h, field);
+    h->buf[1] = dev_alloc(h, field);
+    h->flag_dev = static_cast<int*>(dev_alloc(h, 256));
+    const long long total = (long long)nx * ny;
+    h->diag_nblocks = diag_blocks(total, h->num_sms);
+    h->diag_part = static_cast<double*>(dev_alloc(h, (size_t)h->diag_nblocks * kDiagParts * sizeof(double)));
+    h->diag_out = static_cast<double*>(dev_alloc(h, 256));
+    if (dtype != KBC_F64 && variant != KBC_LBGK)
+        h->fix = static_cast<int*>(dev_alloc(h, (size_t)(64 + total) * sizeof(int)));
+    if (!h->buf[0] || !h->buf[1] || !h->flag_dev || !h->diag_part || !h->diag_out ||
+        (dtype != KBC_F64 && variant != KBC_LBGK && !h->fix)) {
+        kbc_destroy(h);
+        return fail(nullptr, KBC_ERR_NOMEM, "device allocation failed");
+    }
+    e = cudaHostAlloc((void**)&h->flag_host, 4 * sizeof(int), cudaHostAllocDefault);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        h->flag_host = nullptr;
+        kbc_destroy(h);
+        return fail(nullptr, KBC_ERR_CUDA, "pinned allocation failed");
+    }
+    h->flag_host[0] = h->flag_host[1] = h->flag_host[2] = h->flag_host[3] = 0;
+    e = cudaMemsetAsync(h->flag_dev, 0, 256, h->stream);
+    if (e == cudaSuccess && h->fix) e = cudaMemsetAsync(h->fix, 0, 64 * sizeof(int), h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        std::string m = std::string("initial memset: ") + cudaGetErrorString(e);
+        kbc_destroy(h);
+        return fail(nullptr, KBC_ERR_CUDA, m);
+    }
+    *out = h;
+    return KBC_OK;
+}
+
+int kbc_destroy(kbc_handle h)
+{
+    if (!h) return KBC_ERR_ARG;
+    cudaSetDevice(h->device);
+    cudaStreamSynchronize(h->stream);
+    dev_free(h, h->buf[0]);
+    dev_free(h, h->buf[1]);
+    dev_free(h, h->fix);
+    dev_free(h, h->flag_dev);
+    dev_free(h, h->diag_part);
+    dev_free(h, h->diag_out);
+    dev_free(h, h->stage);
+    if (h->flag_host) cudaFreeHost(h->flag_host);
+    cudaGetLastError();
+    delete h;
+    return KBC_OK;
+}
+
+int kbc_set_stream(kbc_handle h, void* stream)
+{
+    if (!h) return KBC_ERR_ARG;
+    h->stream = static_cast<cudaStream_t>(stream);
+    return KBC_OK;
+}
+
+int kbc_set_gamma_mode(kbc_handle h, int mode, double gamma_fixed)
+{
+    if (!h) return KBC_ERR_ARG;
+    if (mode != KBC_GAMMA_ENTROPIC && mode != KBC_GAMMA_FIXED)
+        return fail(h, KBC_ERR_ARG, "bad gamma mode");
+    if (mode == KBC_GAMMA_FIXED && !std::isfinite(gamma_fixed))
+        return fail(h, KBC_ERR_ARG, "gamma must be finite");
+    h->gamma_mode = mode;
+    h->gamma_fixed = gamma_fixed;
+    return KBC_OK;
+}
+
+int kbc_set_guard(kbc_handle h, double threshold)
+{
+    if (!h) return KBC_ERR_ARG;
+    if (!(threshold >= 0.0)) return fail(h, KBC_ERR_ARG, "guard must be >= 0");
+    if (threshold > 0.0 && h->dtype != KBC_F64 && h->variant != KBC_LBGK && !h->fix) {
+        h->fix = static_cast<int*>(dev_alloc(h, (size_t)(64 + (long long)h->nx * h->ny) * sizeof(int)));
+        if (!h->fix) return fail(h, KBC_ERR_NOMEM, "guard list allocation failed");
+        cudaError_t e = cudaMemsetAsync(h->fix, 0, 64 * sizeof(int), h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "memset");
+    }
+    h->guard = threshold;
+    return KBC_OK;
+}
+
+int kbc_guard_count(kbc_handle h, long long* count)
+{
+    int rc = check_h(h);
+    if (rc) return rc;
+    if (!count) return fail(h, KBC_ERR_ARG, "NULL output");
+    *count = 0;
+    if (!h->fix) return KBC_OK;
+    // the last step used slot fix_slot ^ 1 (the slot flips after every step)
+    cudaError_t e = cudaMemcpyAsync(h->flag_host + 2, h->fix + (h->fix_slot ^ 1), sizeof(int),
+                                    cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "guard count copy");
+    rc = wait_stream(h, 0);
+    if (rc) return rc;
+    *count = h->flag_host[2];
+    return KBC_OK;
+}
+
+int kbc_set_f16_scale(kbc_handle h, double scale)
+{
+    if (!h) return KBC_ERR_ARG;
+    if (!(scale > 0.0 && std::isfinite(scale))) return fail(h, KBC_ERR_ARG, "scale must be > 0");
+    if (h->initialized) return fail(h, KBC_ERR_STATE, "set the scale before kbc_init");
+    h->f16_scale = (float)scale;
+    return KBC_OK;
+}
+
+int kbc_init(kbc_handle h, const double* rho, const double* u)
+{
+    return init_common(h, rho, u, false);
+}
+
+int kbc_init_grad(kbc_handle h, const double* rho, const double* u)
+{
+    return init_common(h, rho, u, true);
+}
+
+int kbc_set_populations(kbc_handle h, const double* f)
+{
+    int rc = check_h(h);
+    if (rc) return rc;
+    if (!f) return fail(h, KBC_ERR_ARG, "NULL field");
+    const void* df;
+    rc = stage_in(h, f, (size_t)9 * h->nx * h->ny * sizeof(double), &df);
+    if (rc) return rc;
+    StepArgs a = args_of(h);
+    cudaError_t e = by_codec(h->dtype, [&](auto c) {
+        using C = decltype(c);
+        return launch_set<C>(static_cast<const double*>(df), h->buf[h->cur], a, h->stream, h->num_sms);
+    });
+    if (e != cudaSuccess) return cuda_fail(h, e, "set launch");
+    h->initialized = true;
+    return KBC_OK;
+}
+
+int kbc_get_populations(kbc_handle h, double* f)
+{
+    int rc = check_h(h);
+    if (rc) return rc;
+    if (!f) return fail(h, KBC_ERR_ARG, "NULL field");
+    if (!h->initialized) return fail(h, KBC_ERR_STATE, "field not initialised");
+    const size_t n = (size_t)h->nx * h->ny;
+    StepArgs a = args_of(h);
+    return produce(h, f, 9 * n * sizeof(double), [&](void* t) {
+        return by_codec(h->dtype, [&](auto c) {
+            using C = decltype(c);
+            return launch_get<C>(h->buf[h->cur], static_cast<double*>(t), a, h->stream, h->num_sms);
+        });
+    });
+}
+
+int kbc_step(kbc_handle h, int nsteps)
+{
+    int rc = check_h(h);
+    if (rc) return rc;
+    if (nsteps < 0) return fail(h, KBC_ERR_ARG, "nsteps must be >= 0");
+    if (!h->initialized) return fail(h, KBC_ERR_STATE, "field not initialised");
+    if (*h->flag_host) return fail(h, KBC_ERR_NONFINITE, "non-finite populations detected");
+    if (nsteps == 0) return KBC_OK;
+    Launch L;
+    L.variant = h->variant;
+    L.rows = (h->nx % (32 * vec_width(h->dtype))) == 0;
+    L.stream = h->stream;
+    L.num_sms = h->num_sms;
+    const bool guard_on = h->dtype != KBC_F64 && h->variant != KBC_LBGK &&
+                          h->gamma_mode == KBC_GAMMA_ENTROPIC && h->guard > 0.0 && h->fix;
+    L.fixup = guard_on;
+    for (int s = 0; s < nsteps; ++s) {
+        L.src = h->buf[h->cur];
+        L.dst = h->buf[h->cur ^ 1];
+        L.a = args_of(h);
+        if (!guard_on) {
+            L.a.fix_list = nullptr;
+        }
+        cudaError_t e = by_codec(h->dtype, [&](auto c) {
+            using C = decltype(c);
+            return launch_step<C>(L);
+        });
+        if (e != cudaSuccess) return cuda_fail(h, e, "step launch");
+        h->cur ^= 1;
+        if (guard_on) h->fix_slot ^= 1;
+    }
+    cudaError_t e = cudaMemcpyAsync(h->flag_host, h->flag_dev, sizeof(int), cudaMemcpyDeviceToHost,
+                                    h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "flag copy");
+    return KBC_OK;
+}
+
+int kbc_sync(kbc_handle h, double timeout_s)
+{
+    int rc = check_h(h);
+    if (rc) return rc;
+    rc = wait_stream(h, timeout_s);
+    if (rc) return rc;
+    if (*h->flag_host) return fail(h, KBC_ERR_NONFINITE, "non-finite populations detected");
+    return KBC_OK;
+}
+
+int kbc_probe(kbc_handle h, int count, const long long* nodes, double* f)
+{
+    int rc = check_h(h);
+    if (rc) return rc;
+    if (count < 0 || (count > 0 && (!nodes || !f))) return fail(h, KBC_ERR_ARG, "bad probe arguments");
+    if (!h->initialized) return fail(h, KBC_ERR_STATE, "field not initialised");
+    if (count == 0) return KBC_OK;
+    const bool dn = is_device_ptr(nodes), df = is_device_ptr(f);
+    const size_t nb = (size_t)count * sizeof(long long), fb = (size_t)count * 9 * sizeof(double);
+    const size_t need = 256 + (dn ? 0 : nb) + (df ? 0 : fb);
+    if (h->stage_bytes < need) {
+        dev_free(h, h->stage);
+        h->stage = dev_alloc(h, need);
+        h->stage_bytes = h->stage ? need : 0;
+        if (!h->stage) return fail(h, KBC_ERR_NOMEM, "staging allocation failed");
+    }
+    char* st = static_cast<char*>(h->stage);
+    int* bad = reinterpret_cast<int*>(st);
+    const long long* dnodes = nodes;
+    double* dfo = f;
+    size_t off = 256;
+    if (!dn) {
+        dnodes = reinterpret_cast<const long long*>(st + off);
+        off += nb;
+    }
+    if (!df) dfo = reinterpret_cast<double*>(st + off);
+    cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(int), h->stream);
+    if (e == cudaSuccess && !dn)
+        e = cudaMemcpyAsync((void*)dnodes, nodes, nb, cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "probe upload");
+    StepArgs a = args_of(h);
+    e = by_codec(h->dtype, [&](auto c) {
+        using C = decltype(c);
+        return launch_probe<C>(h->buf[h->cur], dnodes, count, dfo, bad, a, h->stream, h->num_sms);
+    });
+    if (e != cudaSuccess) return cuda_fail(h, e, "probe launch");
+    if (!df) {
+        e = cudaMemcpyAsync(f, dfo, fb, cudaMemcpyDeviceToHost, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "probe download");
+    }
+    int bad_host = 0;
+    e = cudaMemcpyAsync(h->flag_host + 1, bad, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "probe status");
+    rc = wait_stream(h, 0);
+    if (rc) return rc;
+    bad_host = h->flag_host[1];
+    if (bad_host) return fail(h, KBC_ERR_ARG, "probe node index out of range");
+    return KBC_OK;
+}
+
+int kbc_moments(kbc_handle h, double* rho, double* u)
+{
+    int rc = check_h(h);
+    if (rc) return rc;
+    if (!rho || !u) return fail(h, KBC_ERR_ARG, "NULL field");
+    if (!h->initialized) return fail(h, KBC_ERR_STATE, "field not initialised");
+    const size_t n = (size_t)h->nx * h->ny;
+    StepArgs a = args_of(h);
+    const bool dr = is_device_ptr(rho), du = is_device_ptr(u);
+    if (dr && du) {
+        cudaError_t e = by_codec(h->dtype, [&](auto c) {
+            using C = decltype(c);
+            return launch_moments<C>(h->buf[h->cur], rho, u, u + n, a, h->stream, h->num_sms);
+        });
+        return e == cudaSuccess ? KBC_OK : cuda_fail(h, e, "moments launch");
+    }
+    // at least one host output: compute all three fields into staging
+    const size_t bytes = 3 * n * sizeof(double);
+    if (h->stage_bytes < bytes) {
+        dev_free(h, h->stage);
+        h->stage = dev_alloc(h, bytes);
+        h->stage_bytes = h->stage ? bytes : 0;
+        if (!h->stage) return fail(h, KBC_ERR_NOMEM, "staging allocation failed");
+    }
+    double* st = static_cast<double*>(h->stage);
+    cudaError_t e = by_codec(h->dtype, [&](auto c) {
+        using C = decltype(c);
+        return launch_moments<C>(h->buf[h->cur], st, st + n, st + 2 * n, a, h->stream, h->num_sms);
+    });
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(rho, st, n * sizeof(double), cudaMemcpyDefault, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(u, st + n, 2 * n * sizeof(double), cudaMemcpyDefault, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "moments");
+    return wait_stream(h, 0);
+}
+
+int kbc_diagnostics(kbc_handle h, double* out)
+{
+    int rc = check_h(h);
+    if (rc) return rc;
+    if (!out) return fail(h, KBC_ERR_ARG, "NULL output");
+    if (!h->initialized) return fail(h, KBC_ERR_STATE, "field not initialised");
+    StepArgs a = args_of(h);
+    a.guard = 0.0;
+    cudaError_t e = by_codec(h->dtype, [&](auto c) {
+        using C = decltype(c);
+        return launch_diag<C>(h->buf[h->cur], h->diag_part, h->diag_nblocks, h->diag_out,
+                              h->variant, a, h->stream);
+    });
+    if (e != cudaSuccess) return cuda_fail(h, e, "diagnostics launch");
+    e = cudaMemcpyAsync(out, h->diag_out, KBC_DIAG_N * sizeof(double), cudaMemcpyDefault, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "diagnostics copy");
+    return wait_stream(h, 0);
+}
+
+int kbc_bytes_per_update(kbc_handle h, double* bytes)
+{
+    if (!h || !bytes) return KBC_ERR_ARG;
+    *bytes = 18.0 * (double)h->elem;
+    return KBC_OK;
+}
+
+const char* kbc_last_error(kbc_handle h)
+{
+    return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,210 @@
+// Per-node collision of the D2Q9 KBC / LBGK model, register-only.
+//
+// Input d[9] holds the pre-collision populations as deviations
+// d_i = f_i - W_i; on return it holds the post-collision deviations.
+//
+// Steps (Bosch, Chikatamarla, Karlin):
+//   rho = sum f, rho u = sum v f                                  (Sec. 1)
+//   f^eq from Eq. Eq, formed directly as the deviation f^eq - W
+//   df = f - f^eq
+//   second moments of df; because df carries no mass and no momentum,
+//   its central and natural second moments coincide, so only the basis
+//   vectors below depend on the variant (Table 1, Eq. cm)
+//   ds = the population carrying the variant's shear-moment deviations and
+//        no other moment (central basis about u for A/B, natural for C/D;
+//        this is Eq. momentsD2Q9 restricted to the s group, written with the
+//        dual vectors E_pq(c) = e_p(c_x) x e_q(c_y) of the 1-D moment basis)
+//   dh = df - ds                            (k carries no deviation, Sec. 5)
+//   gamma* = 1/beta - (2 - 1/beta) <ds|dh>/<dh|dh>               (Eq. result21)
+//   f' = f - beta (2 ds + gamma dh)                    (Eq. ksh-mirror in Eq. Egeneral)
+// The last line is evaluated in the generalised-equilibrium arrangement of
+// Eq. EGE / Eq. GE,
+//   f' = f - 2 beta df - beta (gamma - 2) dh,
+// so that gamma = 2 removes the h term exactly and reproduces the LBGK
+// update f - 2 beta df (Eq. LBGKmirr) bit for bit.
+#pragma once
+
+#include "kbc_lattice.cuh"
+
+namespace kbc {
+
+// Table 1
+enum : int { kLBGK = 0, kA = 1, kB = 2, kC = 3, kD = 4 };
+
+template <typename T>
+struct CollideParams {
+    T two_beta;        // 2 beta
+    T one_m_2beta;     // 1 - 2 beta
+    T inv_beta;        // 1 / beta
+    T two_m_inv_beta;  // 2 - 1 / beta
+    T ch_fixed;        // beta (gamma_fixed - 2)
+    T gamma_fixed;
+    T guard;           // threshold on rho <dh|dh>; <= 0 disables
+    int fixed;         // 1: gamma = gamma_fixed
+};
+
+template <typename T>
+__host__ CollideParams<T> make_params(double beta, int fixed, double gamma_fixed, double guard)
+{
+    CollideParams<T> p;
+    p.two_beta = (T)(2.0 * beta);
+    p.one_m_2beta = (T)(1.0 - 2.0 * beta);
+    p.inv_beta = (T)(1.0 / beta);
+    p.two_m_inv_beta = (T)(2.0 - 1.0 / beta);
+    p.ch_fixed = (T)(beta * (gamma_fixed - 2.0));
+    p.gamma_fixed = (T)gamma_fixed;
+    p.guard = (T)guard;
+    p.fixed = fixed;
+    return p;
+}
+
+// reciprocal used for the entropic weights (ratio of two sums, so a few ulp
+// do not matter); the velocity uses the correctly rounded rcpT
+template <typename T> __device__ __forceinline__ T rcp_weight(T x);
+template <> __device__ __forceinline__ float rcp_weight<float>(float x) { return __fdividef(1.0f, x); }
+template <> __device__ __forceinline__ double rcp_weight<double>(double x) { return 1.0 / x; }
+
+template <typename T> __device__ __forceinline__ T ratio(T a, T b);
+template <> __device__ __forceinline__ float ratio<float>(float a, float b) { return __fdiv_rn(a, b); }
+template <> __device__ __forceinline__ double ratio<double>(double a, double b) { return a / b; }
+
+// xi_i = v_i . u for a compile-time velocity (a, b)
+template <int A, int B, typename T>
+__device__ __forceinline__ T vdot(T ux, T uy)
+{
+    if constexpr (A == 0 && B == 0) return T(0);
+    else if constexpr (A == 0) return B > 0 ? uy : -uy;
+    else if constexpr (B == 0) return A > 0 ? ux : -ux;
+    else return (A > 0 ? ux : -ux) + (B > 0 ? uy : -uy);
+}
+
+template <int I, typename T>
+__device__ __forceinline__ void eq_dev(T ux, T uy, T usq15, T rho, T drho, T d, T& P, T& df)
+{
+    constexpr int A = I % 3 - 1, B = I / 3 - 1;
+    if constexpr (A == 0 && B == 0) {
+        P = -usq15;
+    } else {
+        const T xi = vdot<A, B>(ux, uy);
+        P = fmaT(xi, fmaT(T(4.5), xi, T(3)), -usq15);   // 3 xi + 4.5 xi^2 - 1.5 u^2
+    }
+    const T deq = T(wgt(I)) * fmaT(rho, P, drho);      // f^eq - W = W (rho - 1 + rho P)
+    df = d - deq;
+}
+
+// Returns gamma; rho_out receives rho (NaN/Inf flags a blown-up node);
+// guard_hit is set when the entropic denominator falls to or below the guard.
+template <int VAR, typename T>
+__device__ __forceinline__ T collide(T (&d)[9], const CollideParams<T>& p, T& rho_out,
+                                     bool& guard_hit)
+{
+    const T drho = ((d[0] + d[8]) + (d[2] + d[6])) + ((d[1] + d[7]) + (d[3] + d[5])) + d[4];
+    const T jx = ((d[2] - d[0]) + (d[8] - d[6])) + (d[5] - d[3]);
+    const T jy = ((d[6] - d[0]) + (d[8] - d[2])) + (d[7] - d[1]);
+    const T rho = T(1) + drho;
+    rho_out = rho;
+    const T irho = rcpT(rho);
+    const T ux = jx * irho, uy = jy * irho;
+    const T usq15 = T(1.5) * fmaT(ux, ux, uy * uy);
+
+    T P[9], df[9];
+    eq_dev<0>(ux, uy, usq15, rho, drho, d[0], P[0], df[0]);
+    eq_dev<1>(ux, uy, usq15, rho, drho, d[1], P[1], df[1]);
+    eq_dev<2>(ux, uy, usq15, rho, drho, d[2], P[2], df[2]);
+    eq_dev<3>(ux, uy, usq15, rho, drho, d[3], P[3], df[3]);
+    eq_dev<4>(ux, uy, usq15, rho, drho, d[4], P[4], df[4]);
+    eq_dev<5>(ux, uy, usq15, rho, drho, d[5], P[5], df[5]);
+    eq_dev<6>(ux, uy, usq15, rho, drho, d[6], P[6], df[6]);
+    eq_dev<7>(ux, uy, usq15, rho, drho, d[7], P[7], df[7]);
+    eq_dev<8>(ux, uy, usq15, rho, drho, d[8], P[8], df[8]);
+
+    if constexpr (VAR == kLBGK) {
+        guard_hit = false;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) d[i] = fmaT(-p.two_beta, df[i], d[i]);
+        return T(2);
+    } else {
+        // second moments of df (natural = central, see header)
+        const T corner = (df[0] + df[2]) + (df[6] + df[8]);
+        const T m20 = corner + (df[3] + df[5]);
+        const T m02 = corner + (df[1] + df[7]);
+        const T m11 = (df[0] + df[8]) - (df[2] + df[6]);
+        // coefficients of E20, E02, E11 in ds: A/C carry T, N, Pi (all three
+        // second moments); B/D carry N and Pi only, i.e. the traceless part
+        // (m20 - m02)/2 (E20 - E02)
+        T c20, c02;
+        if constexpr (VAR == kA || VAR == kC) {
+            c20 = m20;
+            c02 = m02;
+        } else {
+            c20 = T(0.5) * (m20 - m02);
+            c02 = -c20;
+        }
+        T ds[9];
+        if constexpr (VAR == kA || VAR == kB) {
+            // 1-D dual vectors about c: e0(c) = (c(c-1)/2, 1-c^2, c(c+1)/2),
+            // e1(c) = (c-1/2, -2c, c+1/2), e2 = (1/2, -1, 1/2)
+            const T hx = T(0.5) * ux, hy = T(0.5) * uy;
+            const T e0x[3] = {fmaT(hx, ux, -hx), fmaT(-ux, ux, T(1)), fmaT(hx, ux, hx)};
+            const T e0y[3] = {fmaT(hy, uy, -hy), fmaT(-uy, uy, T(1)), fmaT(hy, uy, hy)};
+            const T e1x[3] = {ux - T(0.5), T(-2) * ux, ux + T(0.5)};
+            const T e1y[3] = {uy - T(0.5), T(-2) * uy, uy + T(0.5)};
+            // ds_(a,b) = c20 e2[a] e0y[b] + c02 e0x[a] e2[b] + m11 e1x[a] e1y[b]
+            T Ab[3], Ba[3], Ca[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                Ab[k] = c20 * e0y[k];
+                Ba[k] = c02 * e0x[k];
+                Ca[k] = m11 * e1x[k];
+            }
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const int a = i % 3, b = i / 3;  // a, b in {0,1,2} <-> {-1,0,1}
+                const T ta = (a == 1) ? -Ab[b] : T(0.5) * Ab[b];
+                const T tb = (b == 1) ? -Ba[a] : T(0.5) * Ba[a];
+                ds[i] = fmaT(Ca[a], e1y[b], ta + tb);
+            }
+        } else {
+            // natural basis (c = 0): e0 = (0,1,0), e1 = (-1/2, 0, 1/2)
+            const T q = T(0.25) * m11;
+            ds[4] = -(c20 + c02);
+            ds[3] = ds[5] = T(0.5) * c20;
+            ds[1] = ds[7] = T(0.5) * c02;
+            ds[0] = ds[8] = q;
+            ds[2] = ds[6] = -q;
+        }
+        T dh[9];
+        T sh = T(0), hh = T(0);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            dh[i] = df[i] - ds[i];
+            // rho / f^eq_i = 1 / (W_i (1 + P_i))
+            const T w = T(inv_wgt(i)) * rcp_weight(T(1) + P[i]);
+            const T t = dh[i] * w;
+            sh = fmaT(ds[i], t, sh);
+            hh = fmaT(dh[i], t, hh);
+        }
+        T ch, gamma;
+        guard_hit = false;
+        if (p.fixed) {
+            ch = p.ch_fixed;
+            gamma = p.gamma_fixed;
+        } else {
+            guard_hit = (p.guard > T(0)) && !(hh > p.guard);
+            if (hh > T(0)) {
+                const T R = ratio(sh, hh);
+                ch = p.one_m_2beta * (T(1) + R);             // beta (gamma - 2)
+                gamma = fmaT(-p.two_m_inv_beta, R, p.inv_beta);
+            } else {
+                // <dh|dh> = 0: dh = 0 and gamma multiplies nothing; report 2
+                ch = T(0);
+                gamma = T(2);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 9; ++i) d[i] = fmaT(-ch, dh[i], fmaT(-p.two_beta, df[i], d[i]));
+        return gamma;
+    }
+}
+
+}  // namespace kbc

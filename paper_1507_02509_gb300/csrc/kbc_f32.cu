@@ -1,0 +1,7 @@
+// Kernel instantiations for the CodecF32 storage codec (see kbc_lattice.cuh).
+#define KBC_CODEC_TU 1
+#include "kbc_launch.cuh"
+
+namespace kbc {
+KBC_DEFINE_CODEC(CodecF32)
+}  // namespace kbc

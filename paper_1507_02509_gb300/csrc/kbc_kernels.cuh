@@ -1,0 +1,486 @@
+// Kernels of the fused pull-stream + collide step and its helpers.
+//
+// Data layout in device memory (one population field):
+//   S f[9][plane], plane >= nx * ny, row-major [ny][nx] inside a plane, x
+//   fastest; plane is padded so every plane starts on a 256-byte boundary.
+// Two fields (A, B) alternate: a step reads A and writes B (pull pattern:
+// f_i(x) = f'_i(x - v_i) with periodic wrap, Eq. Egeneral).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <type_traits>
+
+#include "kbc_collide.cuh"
+
+namespace kbc {
+
+struct StepArgs {
+    int nx, ny;
+    long long plane;     // elements between population planes
+    CodecScale cs;
+    double beta, gamma_fixed, guard;
+    int fixed;
+    int* fix_count;      // two counters, used alternately by successive steps
+    int* fix_list;       // node indices recorded for the FP64 re-evaluation
+    int fix_slot;        // counter used by this step
+    int* flag;           // set to 1 when a node's density is not finite
+};
+
+// ---------------------------------------------------------------- vectors
+
+template <int BYTES> struct RawT;
+template <> struct RawT<16> { using type = uint4; };
+template <> struct RawT<8> { using type = uint2; };
+template <> struct RawT<4> { using type = unsigned int; };
+
+template <class S, int NV>
+struct Vec {
+    static constexpr int kBytes = int(sizeof(S)) * NV;
+    using Raw = typename RawT<kBytes>::type;
+    union U {
+        Raw r;
+        S s[NV];
+    };
+    __device__ __forceinline__ static void load(const S* p, S (&v)[NV])
+    {
+        U u;
+        u.r = __ldg(reinterpret_cast<const Raw*>(p));
+#pragma unroll
+        for (int k = 0; k < NV; ++k) v[k] = u.s[k];
+    }
+    __device__ __forceinline__ static void store(S* p, const S (&v)[NV])
+    {
+        U u;
+#pragma unroll
+        for (int k = 0; k < NV; ++k) u.s[k] = v[k];
+        *reinterpret_cast<Raw*>(p) = u.r;
+    }
+};
+
+template <class S> __device__ __forceinline__ S shfl_up1(S v)
+{
+    if constexpr (sizeof(S) == 2) {
+        return (S)__shfl_up_sync(0xffffffffu, (unsigned)v, 1);
+    } else {
+        return __shfl_up_sync(0xffffffffu, v, 1);
+    }
+}
+template <class S> __device__ __forceinline__ S shfl_down1(S v)
+{
+    if constexpr (sizeof(S) == 2) {
+        return (S)__shfl_down_sync(0xffffffffu, (unsigned)v, 1);
+    } else {
+        return __shfl_down_sync(0xffffffffu, v, 1);
+    }
+}
+
+// warp-aggregated append of node n to the re-evaluation list
+__device__ __forceinline__ void record_fix(bool hit, int n, const StepArgs& a)
+{
+    const unsigned active = __activemask();
+    const unsigned m = __ballot_sync(active, hit);
+    if (m == 0u) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(m) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(a.fix_count + a.fix_slot, __popc(m));
+    base = __shfl_sync(active, base, leader);
+    if (hit) a.fix_list[base + __popc(m & ((1u << lane) - 1u))] = n;
+}
+
+template <typename T>
+__device__ __forceinline__ CollideParams<T> params_of(const StepArgs& a)
+{
+    CollideParams<T> p;
+    p.two_beta = (T)(2.0 * a.beta);
+    p.one_m_2beta = (T)(1.0 - 2.0 * a.beta);
+    p.inv_beta = (T)(1.0 / a.beta);
+    p.two_m_inv_beta = (T)(2.0 - 1.0 / a.beta);
+    p.ch_fixed = (T)(a.beta * (a.gamma_fixed - 2.0));
+    p.gamma_fixed = (T)a.gamma_fixed;
+    p.guard = (T)a.guard;
+    p.fixed = a.fixed;
+    return p;
+}
+
+// ---------------------------------------------------------------- step, rows
+//
+// One thread updates NV consecutive nodes of one row with 16-byte loads and
+// stores per population plane.  Populations moving along x (a = +-1) need
+// the neighbour one element to the left/right: it comes from the adjacent
+// lane by a warp shuffle, and lanes 0 / 31 fetch it from memory (periodic
+// wrap at the row ends).  Requires nx % (32 NV) == 0; a 1-D grid of
+// nbx * ny blocks, nbx = ceil(nx / (BLOCK NV)) blocks per row; warps past
+// the row end exit as a whole.
+template <int VAR, class C, int NV, int BLOCK>
+__global__ void __launch_bounds__(BLOCK)
+step_rows(const typename C::S* __restrict__ src, typename C::S* __restrict__ dst, StepArgs a,
+          int nbx)
+{
+    using S = typename C::S;
+    using T = typename C::T;
+    const int y = blockIdx.x / nbx;
+    const int bx = blockIdx.x - y * nbx;
+    const int x0 = (bx * BLOCK + threadIdx.x) * NV;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && a.fix_count)
+        a.fix_count[a.fix_slot ^ 1] = 0;  // free the other counter for the next step
+    if (x0 >= a.nx) return;               // whole warps only (nx % (32 NV) == 0)
+    const int lane = threadIdx.x & 31;
+    const int ym = (y == 0) ? a.ny - 1 : y - 1;
+    const int yp = (y == a.ny - 1) ? 0 : y + 1;
+    const int xl = (x0 == 0) ? a.nx - 1 : x0 - 1;
+    const int xr = (x0 + NV == a.nx) ? 0 : x0 + NV;
+
+    S raw[9][NV];
+    S edge[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const int ai = i % 3 - 1, bi = i / 3 - 1;
+        const int sy = (bi == 1) ? ym : (bi == -1 ? yp : y);   // source row y - b
+        const S* row = src + (long long)i * a.plane + (long long)sy * a.nx;
+        Vec<S, NV>::load(row + x0, raw[i]);
+        if (ai == 1) {
+            edge[i] = S(0);
+            if (lane == 0) edge[i] = __ldg(row + xl);
+        } else if (ai == -1) {
+            edge[i] = S(0);
+            if (lane == 31) edge[i] = __ldg(row + xr);
+        }
+    }
+    T f[NV][9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const int ai = i % 3 - 1;
+        if (ai == 0) {
+#pragma unroll
+            for (int k = 0; k < NV; ++k) f[k][i] = C::decode(raw[i][k], i, a.cs);
+        } else if (ai == 1) {  // source x - 1
+            S left = shfl_up1(raw[i][NV - 1]);
+            if (lane == 0) left = edge[i];
+            f[0][i] = C::decode(left, i, a.cs);
+#pragma unroll
+            for (int k = 1; k < NV; ++k) f[k][i] = C::decode(raw[i][k - 1], i, a.cs);
+        } else {               // source x + 1
+            S right = shfl_down1(raw[i][0]);
+            if (lane == 31) right = edge[i];
+#pragma unroll
+            for (int k = 0; k < NV - 1; ++k) f[k][i] = C::decode(raw[i][k + 1], i, a.cs);
+            f[NV - 1][i] = C::decode(right, i, a.cs);
+        }
+    }
+    const CollideParams<T> p = params_of<T>(a);
+    bool bad = false;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        T rho;
+        bool hit;
+        collide<VAR>(f[k], p, rho, hit);
+        bad |= !isfinite(rho);
+        if constexpr (VAR != kLBGK) {
+            if (a.fix_list) record_fix(hit, y * a.nx + x0 + k, a);
+        }
+    }
+    if (bad) *a.flag = 1;
+    const long long o = (long long)y * a.nx + x0;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        S out[NV];
+#pragma unroll
+        for (int k = 0; k < NV; ++k) out[k] = C::encode(f[k][i], i, a.cs);
+        Vec<S, NV>::store(dst + (long long)i * a.plane + o, out);
+    }
+}
+
+// ---------------------------------------------------------------- step, nodes
+//
+// One node per thread, any nx, ny; same arithmetic as step_rows.
+template <int VAR, class C>
+__global__ void __launch_bounds__(256)
+step_nodes(const typename C::S* __restrict__ src, typename C::S* __restrict__ dst, StepArgs a)
+{
+    using S = typename C::S;
+    using T = typename C::T;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && a.fix_count) a.fix_count[a.fix_slot ^ 1] = 0;
+    const long long total = (long long)a.nx * a.ny;
+    const CollideParams<T> p = params_of<T>(a);
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < total;
+         n += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(n / a.nx), x = (int)(n - (long long)y * a.nx);
+        T f[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const int ai = i % 3 - 1, bi = i / 3 - 1;
+            int sx = x - ai, sy = y - bi;
+            sx = sx < 0 ? sx + a.nx : (sx >= a.nx ? sx - a.nx : sx);
+            sy = sy < 0 ? sy + a.ny : (sy >= a.ny ? sy - a.ny : sy);
+            f[i] = C::decode(__ldg(src + (long long)i * a.plane + (long long)sy * a.nx + sx), i, a.cs);
+        }
+        T rho;
+        bool hit;
+        collide<VAR>(f, p, rho, hit);
+        if (!isfinite(rho)) *a.flag = 1;
+        if constexpr (VAR != kLBGK) {
+            if (a.fix_list) record_fix(hit, (int)n, a);
+        }
+#pragma unroll
+        for (int i = 0; i < 9; ++i) dst[(long long)i * a.plane + n] = C::encode(f[i], i, a.cs);
+    }
+}
+
+// ---------------------------------------------------------------- FP64 re-evaluation
+//
+// Recomputes, entirely in double, the nodes the step recorded (entropic
+// denominator at or below the guard) from the same source field, and
+// overwrites their stored result.
+template <int VAR, class C>
+__global__ void __launch_bounds__(256)
+step_fixup(const typename C::S* __restrict__ src, typename C::S* __restrict__ dst, StepArgs a)
+{
+    using S = typename C::S;
+    const int count = a.fix_count[a.fix_slot];
+    if (count == 0) return;
+    const CollideParams<double> p = params_of<double>(a);
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < count; t += gridDim.x * blockDim.x) {
+        const int n = a.fix_list[t];
+        const int y = n / a.nx, x = n - y * a.nx;
+        double f[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const int ai = i % 3 - 1, bi = i / 3 - 1;
+            int sx = x - ai, sy = y - bi;
+            sx = sx < 0 ? sx + a.nx : (sx >= a.nx ? sx - a.nx : sx);
+            sy = sy < 0 ? sy + a.ny : (sy >= a.ny ? sy - a.ny : sy);
+            f[i] = C::to_f64(src[(long long)i * a.plane + (long long)sy * a.nx + sx], i, a.cs);
+        }
+        CollideParams<double> q = p;
+        q.guard = 0.0;
+        double rho;
+        bool hit;
+        collide<VAR>(f, q, rho, hit);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) dst[(long long)i * a.plane + n] = C::from_f64(f[i], i, a.cs);
+    }
+}
+
+// ---------------------------------------------------------------- init / io
+
+// f = f^eq(rho, u) (Eq. Eq) stored as deviations from W_i; computed in double.
+template <class C>
+__global__ void init_feq(const double* __restrict__ rho, const double* __restrict__ ux,
+                         const double* __restrict__ uy, typename C::S* __restrict__ dst,
+                         StepArgs a)
+{
+    const long long total = (long long)a.nx * a.ny;
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < total;
+         n += (long long)gridDim.x * blockDim.x) {
+        const double r = rho[n], x = ux[n], y = uy[n];
+        const double usq15 = 1.5 * (x * x + y * y);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const double xi = va(i) * x + vb(i) * y;
+            const double P = xi * (3.0 + 4.5 * xi) - usq15;
+            const double dev = wgt(i) * ((r - 1.0) + r * P);
+            dst[(long long)i * a.plane + n] = C::from_f64(dev, i, a.cs);
+        }
+    }
+}
+
+// Grad's approximation (Eq. Grad) with Pi = Pi^eq + Pi^(1) (Eq. Peq,
+// Eq. P1AC), velocity gradients by periodic central differences.
+template <class C>
+__global__ void init_grad(const double* __restrict__ rho, const double* __restrict__ ux,
+                          const double* __restrict__ uy, typename C::S* __restrict__ dst,
+                          StepArgs a)
+{
+    const long long total = (long long)a.nx * a.ny;
+    const double cs2 = 1.0 / 3.0;
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < total;
+         n += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(n / a.nx), x = (int)(n - (long long)y * a.nx);
+        const long long row = (long long)y * a.nx;
+        const long long xp = row + (x + 1 == a.nx ? 0 : x + 1);
+        const long long xm = row + (x == 0 ? a.nx - 1 : x - 1);
+        const long long yp = (long long)(y + 1 == a.ny ? 0 : y + 1) * a.nx + x;
+        const long long ym = (long long)(y == 0 ? a.ny - 1 : y - 1) * a.nx + x;
+        // du[a][b] = d u_b / d x_a
+        const double dxux = 0.5 * (ux[xp] - ux[xm]), dxuy = 0.5 * (uy[xp] - uy[xm]);
+        const double dyux = 0.5 * (ux[yp] - ux[ym]), dyuy = 0.5 * (uy[yp] - uy[ym]);
+        const double r = rho[n], u0 = ux[n], u1 = uy[n];
+        const double c = r * cs2 / (2.0 * a.beta);
+        // non-equilibrium-shifted stress minus the isotropic part rho cs2 delta
+        const double sxx = r * u0 * u0 - c * 2.0 * dxux;
+        const double syy = r * u1 * u1 - c * 2.0 * dyuy;
+        const double sxy = r * u0 * u1 - c * (dxuy + dyux);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const double vx = va(i), vy = vb(i);
+            const double lin = r * (u0 * vx + u1 * vy) / cs2;
+            const double quad = sxx * (vx * vx - cs2) + syy * (vy * vy - cs2) + 2.0 * sxy * vx * vy;
+            const double fi = wgt(i) * (r + lin + quad / (2.0 * cs2 * cs2));
+            dst[(long long)i * a.plane + n] = C::from_f64(fi - wgt(i), i, a.cs);
+        }
+    }
+}
+
+template <class C>
+__global__ void set_populations(const double* __restrict__ f, typename C::S* __restrict__ dst,
+                                StepArgs a)
+{
+    const long long total = (long long)a.nx * a.ny;
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < total;
+         n += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+            dst[(long long)i * a.plane + n] = C::from_f64(f[(long long)i * total + n] - wgt(i), i, a.cs);
+    }
+}
+
+template <class C>
+__global__ void get_populations(const typename C::S* __restrict__ src, double* __restrict__ f,
+                                StepArgs a)
+{
+    const long long total = (long long)a.nx * a.ny;
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < total;
+         n += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+            f[(long long)i * total + n] = C::to_f64(src[(long long)i * a.plane + n], i, a.cs) + wgt(i);
+    }
+}
+
+// f[k][9] = populations of node nodes[k]; bad indices set *bad and are skipped
+template <class C>
+__global__ void probe_nodes(const typename C::S* __restrict__ src, const long long* __restrict__ nodes,
+                            int count, double* __restrict__ f, int* bad, StepArgs a)
+{
+    const long long total = (long long)a.nx * a.ny;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < count; k += gridDim.x * blockDim.x) {
+        const long long n = nodes[k];
+        if (n < 0 || n >= total) {
+            *bad = 1;
+            continue;
+        }
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+            f[(long long)k * 9 + i] = C::to_f64(src[(long long)i * a.plane + n], i, a.cs) + wgt(i);
+    }
+}
+
+// rho and u of every node in double (from the stored deviations)
+template <class C>
+__device__ __forceinline__ void node_macro(const typename C::S* __restrict__ src, long long n,
+                                           const StepArgs& a, double& rho, double& ux, double& uy)
+{
+    double d[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) d[i] = C::to_f64(src[(long long)i * a.plane + n], i, a.cs);
+    const double drho = ((d[0] + d[8]) + (d[2] + d[6])) + ((d[1] + d[7]) + (d[3] + d[5])) + d[4];
+    const double jx = ((d[2] - d[0]) + (d[8] - d[6])) + (d[5] - d[3]);
+    const double jy = ((d[6] - d[0]) + (d[8] - d[2])) + (d[7] - d[1]);
+    rho = 1.0 + drho;
+    ux = jx / rho;
+    uy = jy / rho;
+}
+
+template <class C>
+__global__ void moments(const typename C::S* __restrict__ src, double* __restrict__ rho,
+                        double* __restrict__ ux, double* __restrict__ uy, StepArgs a)
+{
+    const long long total = (long long)a.nx * a.ny;
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < total;
+         n += (long long)gridDim.x * blockDim.x) {
+        double r, x, y;
+        node_macro<C>(src, n, a, r, x, y);
+        rho[n] = r;
+        ux[n] = x;
+        uy[n] = y;
+    }
+}
+
+// ---------------------------------------------------------------- diagnostics
+//
+// Per block: FP64 partial sums of mass, momentum, |u|^2/2 and its square,
+// w^2/2 and its square, gamma (sum, min, max) over a grid-stride range of
+// nodes, written to part[block][10].  gamma is that of the collision the next
+// step performs, evaluated in double.  Deterministic: fixed grid, fixed
+// reduction order.
+constexpr int kDiagParts = 10;
+constexpr int kDiagBlock = 256;
+
+template <int VAR, class C>
+__global__ void __launch_bounds__(kDiagBlock)
+diag_partial(const typename C::S* __restrict__ src, double* __restrict__ part, StepArgs a)
+{
+    const long long total = (long long)a.nx * a.ny;
+    double acc[kDiagParts] = {0, 0, 0, 0, 0, 0, 0, 0, 1e300, -1e300};
+    const CollideParams<double> p = [&] {
+        CollideParams<double> q = params_of<double>(a);
+        q.guard = 0.0;
+        return q;
+    }();
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < total;
+         n += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(n / a.nx), x = (int)(n - (long long)y * a.nx);
+        double r, ux, uy;
+        node_macro<C>(src, n, a, r, ux, uy);
+        acc[0] += r;
+        acc[1] += r * ux;
+        acc[2] += r * uy;
+        const double ke = 0.5 * (ux * ux + uy * uy);
+        acc[3] += ke;
+        acc[4] += ke * ke;
+        const long long row = (long long)y * a.nx;
+        const long long xp = row + (x + 1 == a.nx ? 0 : x + 1);
+        const long long xm = row + (x == 0 ? a.nx - 1 : x - 1);
+        const long long yp = (long long)(y + 1 == a.ny ? 0 : y + 1) * a.nx + x;
+        const long long ym = (long long)(y == 0 ? a.ny - 1 : y - 1) * a.nx + x;
+        double r1, uxp, uyp, uxm, uym, uxyp, uyyp, uxym, uyym;
+        node_macro<C>(src, xp, a, r1, uxp, uyp);
+        node_macro<C>(src, xm, a, r1, uxm, uym);
+        node_macro<C>(src, yp, a, r1, uxyp, uyyp);
+        node_macro<C>(src, ym, a, r1, uxym, uyym);
+        const double w = 0.5 * (uyp - uym) - 0.5 * (uxyp - uxym);
+        const double zz = 0.5 * w * w;
+        acc[5] += zz;
+        acc[6] += zz * zz;
+        double f[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const int ai = i % 3 - 1, bi = i / 3 - 1;
+            int sx = x - ai, sy = y - bi;
+            sx = sx < 0 ? sx + a.nx : (sx >= a.nx ? sx - a.nx : sx);
+            sy = sy < 0 ? sy + a.ny : (sy >= a.ny ? sy - a.ny : sy);
+            f[i] = C::to_f64(src[(long long)i * a.plane + (long long)sy * a.nx + sx], i, a.cs);
+        }
+        double rr;
+        bool hit;
+        const double g = collide<VAR>(f, p, rr, hit);
+        acc[7] += g;
+        acc[8] = fmin(acc[8], g);
+        acc[9] = fmax(acc[9], g);
+    }
+    __shared__ double sm[kDiagParts][kDiagBlock];
+#pragma unroll
+    for (int k = 0; k < kDiagParts; ++k) sm[k][threadIdx.x] = acc[k];
+    __syncthreads();
+    for (int s = kDiagBlock / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) sm[k][threadIdx.x] += sm[k][threadIdx.x + s];
+            sm[8][threadIdx.x] = fmin(sm[8][threadIdx.x], sm[8][threadIdx.x + s]);
+            sm[9][threadIdx.x] = fmax(sm[9][threadIdx.x], sm[9][threadIdx.x + s]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < kDiagParts; ++k) part[(long long)blockIdx.x * kDiagParts + k] = sm[k][0];
+    }
+}
+
+// Reduces part[nblocks][10] (fixed order) into out[KBC_DIAG_N].
+__global__ void diag_final(const double* __restrict__ part, int nblocks, double* __restrict__ out,
+                           long long total);
+
+}  // namespace kbc

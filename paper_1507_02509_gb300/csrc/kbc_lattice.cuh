@@ -1,0 +1,91 @@
+// D2Q9 lattice constants and storage codecs for the sm_103a kernels.
+//
+// Velocity set (Sec. 2): tensor product of {-1, 0, 1}; population index
+// i = 3(b+1) + (a+1) for v_i = (a, b).  The weights W_i and cs^2 are not
+// printed in the paper (Eq. S, Eq. Eq); the D2Q9 product weights
+// W_(a,b) = w_a w_b with w_0 = 2/3, w_{+-1} = 1/6 and cs^2 = 1/3 are used.
+//
+// Populations are stored as deviations from the rest weights, d_i = f_i - W_i,
+// which keeps O(u) information in the leading bits of low-precision storage.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cstdint>
+
+namespace kbc {
+
+__host__ __device__ constexpr int va(int i) { return i % 3 - 1; }
+__host__ __device__ constexpr int vb(int i) { return i / 3 - 1; }
+__host__ __device__ constexpr double w1(int a) { return a == 0 ? 2.0 / 3.0 : 1.0 / 6.0; }
+__host__ __device__ constexpr double wgt(int i) { return w1(va(i)) * w1(vb(i)); }
+// 1 / W_i: 36 (diagonal), 9 (axis), 9/4 (rest)
+__host__ __device__ constexpr double inv_wgt(int i)
+{
+    return (va(i) != 0 && vb(i) != 0) ? 36.0 : (va(i) == 0 && vb(i) == 0) ? 2.25 : 9.0;
+}
+
+template <typename T> __device__ __forceinline__ T fmaT(T a, T b, T c);
+template <> __device__ __forceinline__ float fmaT<float>(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+template <> __device__ __forceinline__ double fmaT<double>(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// correctly rounded reciprocal
+template <typename T> __device__ __forceinline__ T rcpT(T x);
+template <> __device__ __forceinline__ float rcpT<float>(float x) { return __frcp_rn(x); }
+template <> __device__ __forceinline__ double rcpT<double>(double x) { return __drcp_rn(x); }
+
+// Scale of the half-precision encoding (unused by the other codecs).
+struct CodecScale {
+    float scale;      // S
+    float inv_scale;  // 1 / S
+};
+
+// Storage codecs: S = stored element, T = arithmetic type.
+//   decode(s, i, c)     -> d_i = f_i - W_i in T
+//   encode(d, i, c)     -> stored element
+//   to_f64(s, i, c)     -> d_i in double (exact for F64/F32 storage)
+//   from_f64(d, i, c)   -> stored element from a double deviation
+struct CodecF64 {
+    using S = double;
+    using T = double;
+    static constexpr int kVec = 2;  // elements per 16-byte vector
+    __device__ __forceinline__ static T decode(S s, int, const CodecScale&) { return s; }
+    __device__ __forceinline__ static S encode(T d, int, const CodecScale&) { return d; }
+    __device__ __forceinline__ static double to_f64(S s, int, const CodecScale&) { return s; }
+    __device__ __forceinline__ static S from_f64(double d, int, const CodecScale&) { return d; }
+};
+
+struct CodecF32 {
+    using S = float;
+    using T = float;
+    static constexpr int kVec = 4;
+    __device__ __forceinline__ static T decode(S s, int, const CodecScale&) { return s; }
+    __device__ __forceinline__ static S encode(T d, int, const CodecScale&) { return d; }
+    __device__ __forceinline__ static double to_f64(S s, int, const CodecScale&) { return (double)s; }
+    __device__ __forceinline__ static S from_f64(double d, int, const CodecScale&) { return __double2float_rn(d); }
+};
+
+// (f - W)/W * S in IEEE half (stored as its 16-bit pattern), arithmetic in
+// float.
+struct CodecF16 {
+    using S = unsigned short;
+    using T = float;
+    static constexpr int kVec = 8;
+    __device__ __forceinline__ static T decode(S s, int i, const CodecScale& c)
+    {
+        return __half2float(__ushort_as_half(s)) * ((float)wgt(i) * c.inv_scale);
+    }
+    __device__ __forceinline__ static S encode(T d, int i, const CodecScale& c)
+    {
+        return __half_as_ushort(__float2half_rn(d * ((float)inv_wgt(i) * c.scale)));
+    }
+    __device__ __forceinline__ static double to_f64(S s, int i, const CodecScale& c)
+    {
+        return (double)__half2float(__ushort_as_half(s)) * (wgt(i) * (double)c.inv_scale);
+    }
+    __device__ __forceinline__ static S from_f64(double d, int i, const CodecScale& c)
+    {
+        return __half_as_ushort(__double2half(d * (inv_wgt(i) * (double)c.scale)));
+    }
+};
+
+}  // namespace kbc

@@ -1,0 +1,180 @@
+// Host-side launchers, one explicit instantiation per storage codec
+// (kbc_f64.cu, kbc_f32.cu, kbc_f16.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "kbc_kernels.cuh"
+
+namespace kbc {
+
+struct Launch {
+    const void* src;
+    void* dst;
+    StepArgs a;
+    int variant;
+    bool rows;      // vectorised row kernel (nx % (32 * kVec) == 0)
+    bool fixup;     // FP64 re-evaluation pass after the step
+    cudaStream_t stream;
+    int num_sms;
+};
+
+constexpr int kRowBlock = 128;
+constexpr int kNodeBlock = 256;
+
+inline int grid_for(long long total, int block, int num_sms, int per_sm)
+{
+    long long b = (total + block - 1) / block;
+    long long cap = (long long)num_sms * per_sm;
+    if (b > cap) b = cap;
+    return b < 1 ? 1 : (int)b;
+}
+
+template <int VAR, class C>
+cudaError_t launch_step_v(const Launch& L)
+{
+    using S = typename C::S;
+    const S* src = static_cast<const S*>(L.src);
+    S* dst = static_cast<S*>(L.dst);
+    if (L.rows) {
+        constexpr int NV = C::kVec;
+        const int nbx = (L.a.nx + kRowBlock * NV - 1) / (kRowBlock * NV);
+        step_rows<VAR, C, NV, kRowBlock>
+            <<<(unsigned)((long long)nbx * L.a.ny), kRowBlock, 0, L.stream>>>(src, dst, L.a, nbx);
+    } else {
+        const long long total = (long long)L.a.nx * L.a.ny;
+        step_nodes<VAR, C><<<grid_for(total, kNodeBlock, L.num_sms, 16), kNodeBlock, 0, L.stream>>>(
+            src, dst, L.a);
+    }
+    if constexpr (VAR != kLBGK) {
+        if (L.fixup)
+            step_fixup<VAR, C><<<L.num_sms * 2, kNodeBlock, 0, L.stream>>>(src, dst, L.a);
+    }
+    return cudaGetLastError();
+}
+
+template <class C>
+cudaError_t launch_step(const Launch& L)
+{
+    switch (L.variant) {
+    case kLBGK: return launch_step_v<kLBGK, C>(L);
+    case kA: return launch_step_v<kA, C>(L);
+    case kB: return launch_step_v<kB, C>(L);
+    case kC: return launch_step_v<kC, C>(L);
+    case kD: return launch_step_v<kD, C>(L);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <class C>
+cudaError_t launch_init(const double* rho, const double* ux, const double* uy, void* dst,
+                        const StepArgs& a, bool grad, cudaStream_t s, int num_sms)
+{
+    const long long total = (long long)a.nx * a.ny;
+    const int g = grid_for(total, kNodeBlock, num_sms, 16);
+    if (grad)
+        init_grad<C><<<g, kNodeBlock, 0, s>>>(rho, ux, uy, static_cast<typename C::S*>(dst), a);
+    else
+        init_feq<C><<<g, kNodeBlock, 0, s>>>(rho, ux, uy, static_cast<typename C::S*>(dst), a);
+    return cudaGetLastError();
+}
+
+template <class C>
+cudaError_t launch_set(const double* f, void* dst, const StepArgs& a, cudaStream_t s, int num_sms)
+{
+    const long long total = (long long)a.nx * a.ny;
+    set_populations<C><<<grid_for(total, kNodeBlock, num_sms, 16), kNodeBlock, 0, s>>>(
+        f, static_cast<typename C::S*>(dst), a);
+    return cudaGetLastError();
+}
+
+template <class C>
+cudaError_t launch_get(const void* src, double* f, const StepArgs& a, cudaStream_t s, int num_sms)
+{
+    const long long total = (long long)a.nx * a.ny;
+    get_populations<C><<<grid_for(total, kNodeBlock, num_sms, 16), kNodeBlock, 0, s>>>(
+        static_cast<const typename C::S*>(src), f, a);
+    return cudaGetLastError();
+}
+
+template <class C>
+cudaError_t launch_moments(const void* src, double* rho, double* ux, double* uy,
+                           const StepArgs& a, cudaStream_t s, int num_sms)
+{
+    const long long total = (long long)a.nx * a.ny;
+    moments<C><<<grid_for(total, kNodeBlock, num_sms, 16), kNodeBlock, 0, s>>>(
+        static_cast<const typename C::S*>(src), rho, ux, uy, a);
+    return cudaGetLastError();
+}
+
+template <class C>
+cudaError_t launch_probe(const void* src, const long long* nodes, int count, double* f, int* bad,
+                         const StepArgs& a, cudaStream_t s, int num_sms)
+{
+    probe_nodes<C><<<grid_for(count, kNodeBlock, num_sms, 4), kNodeBlock, 0, s>>>(
+        static_cast<const typename C::S*>(src), nodes, count, f, bad, a);
+    return cudaGetLastError();
+}
+
+// number of partial-sum blocks the diagnostics use for this grid
+inline int diag_blocks(long long total, int num_sms)
+{
+    return grid_for(total, kDiagBlock, num_sms, 4);
+}
+
+template <class C>
+cudaError_t launch_diag(const void* src, double* part, int nblocks, double* out, int variant,
+                        const StepArgs& a, cudaStream_t s)
+{
+    const typename C::S* p = static_cast<const typename C::S*>(src);
+    switch (variant) {
+    case kLBGK: diag_partial<kLBGK, C><<<nblocks, kDiagBlock, 0, s>>>(p, part, a); break;
+    case kA: diag_partial<kA, C><<<nblocks, kDiagBlock, 0, s>>>(p, part, a); break;
+    case kB: diag_partial<kB, C><<<nblocks, kDiagBlock, 0, s>>>(p, part, a); break;
+    case kC: diag_partial<kC, C><<<nblocks, kDiagBlock, 0, s>>>(p, part, a); break;
+    case kD: diag_partial<kD, C><<<nblocks, kDiagBlock, 0, s>>>(p, part, a); break;
+    default: return cudaErrorInvalidValue;
+    }
+    diag_final<<<1, kDiagBlock, 0, s>>>(part, nblocks, out, (long long)a.nx * a.ny);
+    return cudaGetLastError();
+}
+
+// explicit instantiations live in the per-codec translation units
+#define KBC_DECLARE_CODEC(C)                                                                   \
+    extern template cudaError_t launch_step<C>(const Launch&);                                \
+    extern template cudaError_t launch_init<C>(const double*, const double*, const double*,   \
+                                               void*, const StepArgs&, bool, cudaStream_t,    \
+                                               int);                                          \
+    extern template cudaError_t launch_set<C>(const double*, void*, const StepArgs&,          \
+                                              cudaStream_t, int);                             \
+    extern template cudaError_t launch_get<C>(const void*, double*, const StepArgs&,          \
+                                              cudaStream_t, int);                             \
+    extern template cudaError_t launch_moments<C>(const void*, double*, double*, double*,     \
+                                                  const StepArgs&, cudaStream_t, int);        \
+    extern template cudaError_t launch_diag<C>(const void*, double*, int, double*, int,       \
+                                               const StepArgs&, cudaStream_t);                \
+    extern template cudaError_t launch_probe<C>(const void*, const long long*, int, double*,  \
+                                                int*, const StepArgs&, cudaStream_t, int);
+
+#define KBC_DEFINE_CODEC(C)                                                                    \
+    template cudaError_t launch_step<C>(const Launch&);                                       \
+    template cudaError_t launch_init<C>(const double*, const double*, const double*, void*,   \
+                                        const StepArgs&, bool, cudaStream_t, int);            \
+    template cudaError_t launch_set<C>(const double*, void*, const StepArgs&, cudaStream_t,   \
+                                       int);                                                  \
+    template cudaError_t launch_get<C>(const void*, double*, const StepArgs&, cudaStream_t,   \
+                                       int);                                                  \
+    template cudaError_t launch_moments<C>(const void*, double*, double*, double*,            \
+                                           const StepArgs&, cudaStream_t, int);               \
+    template cudaError_t launch_diag<C>(const void*, double*, int, double*, int,              \
+                                        const StepArgs&, cudaStream_t);                       \
+    template cudaError_t launch_probe<C>(const void*, const long long*, int, double*, int*,   \
+                                         const StepArgs&, cudaStream_t, int);
+
+#ifndef KBC_CODEC_TU
+KBC_DECLARE_CODEC(CodecF64)
+KBC_DECLARE_CODEC(CodecF32)
+KBC_DECLARE_CODEC(CodecF16)
+#endif
+
+}  // namespace kbc

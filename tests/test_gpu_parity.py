@@ -1,0 +1,349 @@
+"""GPU parity: the sm_103a stream-collide path against the FP64 CPU oracle.
+
+All inputs are seeded; the oracle always starts from the same (storage-
+representable) populations as the GPU.  Tolerances:
+  f64: populations within 1e-13 absolute after one step, 1e-12 relative
+       velocity after 1000 steps;
+  f32: 2e-6 absolute per population after one step (a few float ulps of
+       f ~ 0.44 plus the float evaluation of the entropic weights), 1e-5
+       relative velocity after 1000 laminar steps;
+  f16: storage rounds to 2^-11 relative of (f - W)/W, so 5e-4 * W_i.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O  # noqa: E402
+from paper_1507_02509_gb300 import KBCError, Lattice, capi, flows  # noqa: E402
+from tests.gpu_helpers import (max_rel_velocity_error, random_field, representable,  # noqa: E402
+                               weights, windows)
+
+pytestmark = pytest.mark.gpu
+
+VARIANTS = ["lbgk", "A", "B", "C", "D"]
+OV = {"lbgk": O.LBGK, "A": O.A, "B": O.B, "C": O.C, "D": O.D}
+TOL1 = {"f64": 1e-13, "f32": 2e-6}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    capi.load()
+
+
+def _one_step(nx, ny, variant, dtype, seed, beta=0.97, steps=1):
+    g = representable(random_field(nx, ny, seed), dtype)
+    lat = Lattice(nx, ny, variant=variant, beta=beta, dtype=dtype)
+    lat.set_populations(g)
+    lat.step(steps)
+    got = lat.populations().cpu().numpy()
+    lat.sync()
+    lat.close()
+    ref = O.step(g, OV[variant], beta, steps)
+    return got, ref
+
+
+# shapes: vector-row kernel over several warps and blocks with a partial last
+# block (640 = 5 x 128 for f32, 10 x 64 for f64), odd row counts, and the
+# per-node kernel for ragged widths; 1 x 1 wraps every population onto itself
+SHAPES = [(640, 37), (768, 6), (37, 23), (130, 5), (3, 3), (1, 1), (2, 7)]
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("shape", SHAPES)
+def test_one_step_matches_oracle(shape, variant, dtype):
+    nx, ny = shape
+    got, ref = _one_step(nx, ny, variant, dtype, seed=nx * 131 + ny)
+    err = np.max(np.abs(got - ref))
+    assert err <= TOL1[dtype], err
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("shape", [(768, 9), (256, 4), (37, 11)])
+def test_one_step_f16(shape, variant):
+    """f16 storage: the GPU result, re-rounded to half, against the oracle
+    result of the same stored input (tolerance: a few half ulps of (f-W)/W)."""
+    nx, ny = shape
+    got, ref = _one_step(nx, ny, variant, "f16", seed=nx + 7 * ny)
+    Wb = weights().reshape(9, 1, 1)
+    rel = np.abs(got - ref) / Wb
+    assert np.max(rel) < 2e-3, np.max(rel)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "f16"])
+@pytest.mark.parametrize("shape", [(768, 8), (37, 5)])
+def test_kbc_gamma_two_is_lbgk_bit_for_bit(dtype, shape):
+    """KBC with gamma forced to 2 gives exactly the LBGK kernel's bits."""
+    nx, ny = shape
+    g = representable(random_field(nx, ny, 5), dtype)
+    outs = {}
+    for v in ("lbgk", "A", "B", "C", "D"):
+        lat = Lattice(nx, ny, variant=v, beta=0.93, dtype=dtype)
+        if v != "lbgk":
+            lat.set_gamma(2.0)
+        lat.set_populations(g)
+        lat.step(3)
+        outs[v] = lat.populations().cpu().numpy()
+        lat.close()
+    for v in "ABCD":
+        assert np.array_equal(outs[v], outs["lbgk"]), v
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("variant", ["lbgk", "A", "B", "C", "D"])
+def test_taylor_green_1000_steps(variant, dtype):
+    """Taylor-Green vortex 64^2, u0 = 0.04, nu = 0.01, equilibrium
+    initialisation: velocity against the oracle after 1000 steps."""
+    n, nu = 64, 0.01
+    beta = 1.0 / (6 * nu + 1)
+    rho, ux, uy = flows.taylor_green(n, u0=0.04)
+    lat = Lattice(n, n, variant=variant, beta=beta, dtype=dtype)
+    lat.init(rho, ux, uy).step(1000)
+    r, vx, vy = (t.cpu().numpy() for t in lat.moments())
+    lat.sync()
+    lat.close()
+    ref = O.step(O.init_feq(rho, ux, uy), OV[variant], beta, 1000, nthreads=8)
+    _, rx, ry = O.macro(ref)
+    err = max_rel_velocity_error((vx, vy), (rx, ry))
+    tol = 1e-12 if dtype == "f64" else 1e-5
+    assert err < tol, err
+    # and the vortex decays at the rate set by Eq. viscosity (2% at 64^2)
+    k = 2 * math.pi / n
+    amp = np.sum(vx * ux) / np.sum(ux * ux)
+    assert amp == pytest.approx(math.exp(-2 * nu * k * k * 1000), rel=2e-2)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_shear_layer_1024(dtype):
+    """Doubly periodic shear layer 1024^2 (u0 = 0.04, kappa = 80, delta = 0.05,
+    Re = 30000), KBC B: velocity error against the oracle at steps 100 and
+    1000."""
+    n = 1024
+    nu = 0.04 * n / 30000.0
+    beta = 1.0 / (6 * nu + 1)
+    rho, ux, uy = flows.shear_layer(n)
+    lat = Lattice(n, n, variant="B", beta=beta, dtype=dtype)
+    lat.init(rho, ux, uy)
+    g = O.init_feq(rho, ux, uy)
+    done = 0
+    for target, tol in ((100, 1e-12 if dtype == "f64" else 1e-5),
+                        (1000, 1e-11 if dtype == "f64" else 1e-4)):
+        lat.step(target - done)
+        g = O.step(g, O.B, beta, target - done, nthreads=16)
+        done = target
+        _, vx, vy = (t.cpu().numpy() for t in lat.moments())
+        _, rx, ry = O.macro(g)
+        err = max_rel_velocity_error((vx, vy), (rx, ry))
+        print(f"shear layer {dtype} step {target}: max rel velocity error {err:.3e}")
+        assert err < tol, (target, err)
+    lat.close()
+
+
+def test_turbulence_4096_sampled():
+    """Decaying turbulence 4096^2 (E(k) ~ k^4 exp(-2 (k/16)^2), u_rms = 0.03,
+    Re = 1e5), KBC B in f32 and f64: populations at 48 seeded nodes after 10
+    steps against the oracle run on periodic windows around each node."""
+    n, steps = 4096, 10
+    nu = n * 0.03 / 1e5
+    beta = 1.0 / (6 * nu + 1)
+    rho, ux, uy = flows.turbulence(n, k0=16, urms=0.03, seed=2024)
+    rng = np.random.default_rng(1)
+    xy = [(int(x), int(y)) for x, y in zip(rng.integers(0, n, 48), rng.integers(0, n, 48))]
+    xy += [(0, 0), (n - 1, n - 1), (0, n - 1), (n - 1, 0)]
+    nodes = [y * n + x for x, y in xy]
+    ref = windows(lambda xs, ys: O.init_feq(rho[np.ix_(ys, xs)], ux[np.ix_(ys, xs)],
+                                            uy[np.ix_(ys, xs)]),
+                  n, n, xy, steps, O.B, beta)
+    for dtype, tol in (("f64", 1e-13), ("f32", 3e-6)):
+        lat = Lattice(n, n, variant="B", beta=beta, dtype=dtype)
+        lat.init(rho, ux, uy).step(steps)
+        got = lat.probe(nodes)
+        lat.close()
+        err = np.max(np.abs(got - ref))
+        assert err < tol, (dtype, err)
+
+
+def test_full_size_16384_f32_sampled():
+    """The benchmark's launch configuration: 16384^2, f32 storage, KBC B,
+    vector-row kernel with the FP64 guard pass.  A Taylor-Green field with
+    seeded noise (cheap to build at this size) is advanced 6 steps; 40 sampled
+    nodes, the four corners and row ends are checked against windowed oracle
+    runs."""
+    n, steps, beta = 16384, 6, 0.9995
+    rng = np.random.default_rng(77)
+    x = np.arange(n)
+    k = 2 * math.pi * 8 / n
+
+    def field(xs, ys):
+        X, Y = np.meshgrid(xs.astype(np.float64), ys.astype(np.float64))
+        ux = -0.03 * np.cos(k * X) * np.sin(k * Y)
+        uy = 0.03 * np.sin(k * X) * np.cos(k * Y)
+        return ux, uy
+
+    noise_x = 0.002 * rng.standard_normal((n, n))
+    noise_y = 0.002 * rng.standard_normal((n, n))
+    ux, uy = field(x, x)
+    ux += noise_x
+    uy += noise_y
+    rho = np.ones((n, n))
+    xy = [(int(a), int(b)) for a, b in zip(rng.integers(0, n, 40), rng.integers(0, n, 40))]
+    xy += [(0, 0), (n - 1, n - 1), (0, n - 1), (n - 1, 0), (127, 5), (128, 5), (n - 128, 9)]
+    ref = windows(lambda xs, ys: O.init_feq(rho[np.ix_(ys, xs)], ux[np.ix_(ys, xs)],
+                                            uy[np.ix_(ys, xs)]),
+                  n, n, xy, steps, O.B, beta)
+    lat = Lattice(n, n, variant="B", beta=beta, dtype="f32")
+    lat.init(rho, ux, uy)
+    del noise_x, noise_y
+    lat.step(steps)
+    got = lat.probe([b * n + a for a, b in xy])
+    lat.sync()
+    lat.close()
+    assert np.max(np.abs(got - ref)) < 3e-6
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "f16"])
+def test_uniform_flow_fixed_point(dtype):
+    n = 256
+    rho = np.full((8, n), 1.02)
+    ux = np.full((8, n), 0.05)
+    uy = np.full((8, n), -0.02)
+    for v in VARIANTS:
+        lat = Lattice(n, 8, variant=v, beta=0.99, dtype=dtype)
+        lat.init(rho, ux, uy)
+        f0 = lat.populations().cpu().numpy()
+        lat.step(10)
+        f1 = lat.populations().cpu().numpy()
+        lat.close()
+        tol = {"f64": 2e-16, "f32": 3e-8, "f16": 1e-4}[dtype]
+        assert np.max(np.abs(f1 - f0)) <= tol, (v, np.max(np.abs(f1 - f0)))
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_conservation_f64(variant):
+    nx, ny = 384, 20
+    g = random_field(nx, ny, 3)
+    lat = Lattice(nx, ny, variant=variant, beta=0.995, dtype="f64")
+    lat.set_populations(g)
+    d0 = lat.diagnostics()
+    lat.step(50)
+    d1 = lat.diagnostics()
+    lat.close()
+    assert abs(d1["mass"] - d0["mass"]) <= 1e-13 * d0["mass"]
+    assert abs(d1["px"] - d0["px"]) <= 1e-13 * d0["mass"]
+    assert abs(d1["py"] - d0["py"]) <= 1e-13 * d0["mass"]
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("variant", ["lbgk", "B", "C"])
+def test_diagnostics_and_moments_match_oracle(variant, dtype):
+    nx, ny = 256, 33
+    g = representable(random_field(nx, ny, 11), dtype)
+    lat = Lattice(nx, ny, variant=variant, beta=0.96, dtype=dtype)
+    lat.set_populations(g)
+    d = lat.diagnostics()
+    r, vx, vy = (t.cpu().numpy() for t in lat.moments())
+    lat.close()
+    ref = O.diagnostics(g, OV[variant], 0.96)
+    got = np.array([d[k] for k in O.DIAG_NAMES])
+    assert np.allclose(got, ref, rtol=1e-12, atol=1e-14), (got, ref)
+    rr, rx, ry = O.macro(g)
+    assert np.allclose(r, rr, rtol=0, atol=1e-15)
+    assert np.allclose(vx, rx, rtol=0, atol=1e-15)
+    assert np.allclose(vy, ry, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_grad_initialisation_matches_oracle(dtype):
+    n, beta = 256, 0.95
+    rho, ux, uy = flows.turbulence(n, k0=5, urms=0.04, seed=9, kcut=40)
+    lat = Lattice(n, n, variant="B", beta=beta, dtype=dtype)
+    lat.init(rho, ux, uy, grad=True)
+    got = lat.populations().cpu().numpy()
+    lat.close()
+    ref = representable(O.init_grad(beta, rho, ux, uy), dtype)
+    assert np.max(np.abs(got - ref)) < (1e-16 if dtype == "f64" else 1e-9)
+
+
+def test_guard_pass_recomputes_in_fp64():
+    """A field that is uniform except for a sheared band: in the uniform part
+    <dh|dh> falls below the guard and those nodes are recomputed in FP64; the
+    result is compared with the oracle, with the guard on and off."""
+    nx, ny, beta = 512, 16, 0.999
+    rho = np.ones((ny, nx))
+    ux = np.full((ny, nx), 0.04)
+    uy = np.zeros((ny, nx))
+    ux[6:10, :] += 0.01 * np.sin(2 * math.pi * np.arange(nx) / nx)[None, :]
+    g = O.init_feq(rho, ux, uy)
+    g32 = representable(g, "f32")
+    ref = O.step(g32, O.B, beta, 2)
+    errs = {}
+    for guard in (1e-12, 0.0):
+        lat = Lattice(nx, ny, variant="B", beta=beta, dtype="f32")
+        lat.set_guard(guard)
+        lat.set_populations(g32)
+        lat.step(2)
+        got = lat.populations().cpu().numpy()
+        lat.close()
+        errs[guard] = np.max(np.abs(got - ref))
+    assert errs[1e-12] < 2e-6, errs
+    assert errs[1e-12] <= errs[0.0] + 1e-12, errs
+
+
+def test_nonfinite_is_reported_not_trapped():
+    """A NaN planted in the input is detected by the step's canary: kbc_sync
+    reports KBC_ERR_NONFINITE and the context stays usable."""
+    nx, ny = 256, 4
+    g = random_field(nx, ny, 1)
+    g[4, 2, 17] = np.nan
+    lat = Lattice(nx, ny, variant="B", beta=0.9, dtype="f32")
+    lat.set_populations(g)
+    lat.step(1)
+    with pytest.raises(KBCError) as ei:
+        lat.sync()
+    assert ei.value.status == capi.KBC_ERR_NONFINITE
+    with pytest.raises(KBCError):
+        lat.step(1)
+    lat.close()
+    ok = Lattice(nx, ny, variant="B", beta=0.9, dtype="f32")
+    ok.set_populations(random_field(nx, ny, 2))
+    ok.step(2)
+    ok.sync()
+    ok.close()
+
+
+def test_argument_errors():
+    with pytest.raises(KBCError) as e:
+        capi.kbc_create(0, 4, 1, 0.9, 1)
+    assert e.value.status == capi.KBC_ERR_ARG
+    with pytest.raises(KBCError):
+        capi.kbc_create(4, 4, 7, 0.9, 1)
+    with pytest.raises(KBCError):
+        capi.kbc_create(4, 4, 1, 1.5, 1)
+    lat = Lattice(64, 4, variant="B", beta=0.9, dtype="f32")
+    with pytest.raises(KBCError) as e:
+        lat.step(1)  # before init
+    assert e.value.status == capi.KBC_ERR_STATE
+    lat.set_populations(random_field(64, 4, 0))
+    with pytest.raises(KBCError):
+        lat.probe([64 * 4])
+    lat.close()
+
+
+def test_host_and_device_pointers_agree():
+    n = 256
+    rho, ux, uy = flows.taylor_green(n, u0=0.03)
+    a = Lattice(n, n, variant="A", beta=0.97, dtype="f32")
+    a.init(rho, ux, uy).step(20)
+    b = Lattice(n, n, variant="A", beta=0.97, dtype="f32")
+    b.init(*(torch.as_tensor(v, device="cuda") for v in (rho, ux, uy))).step(20)
+    ra, xa, ya = (t.cpu().numpy() for t in a.moments())
+    h_rho = np.empty((n, n))
+    h_u = np.empty((2, n, n))
+    capi.kbc_moments(b.h, h_rho, h_u)
+    assert np.array_equal(ra, h_rho) and np.array_equal(xa, h_u[0]) and np.array_equal(ya, h_u[1])
+    a.close()
+    b.close()
