@@ -152,10 +152,11 @@ StepArgs args_of(const kbc_ctx* h)
     a.plane = h->plane;
     a.cs.scale = h->f16_scale;
     a.cs.inv_scale = 1.0f / h->f16_scale;
+    const int fixed = (h->gamma_mode == KBC_GAMMA_FIXED) ? 1 : 0;
+    const double guard = (h->dtype == KBC_F64) ? 0.0 : h->guard;
+    a.pf = make_params<float>(h->beta, fixed, h->gamma_fixed, guard);
+    a.pd = make_params<double>(h->beta, fixed, h->gamma_fixed, guard);
     a.beta = h->beta;
-    a.fixed = (h->gamma_mode == KBC_GAMMA_FIXED) ? 1 : 0;
-    a.gamma_fixed = h->gamma_fixed;
-    a.guard = (h->dtype == KBC_F64) ? 0.0 : h->guard;
     a.fix_count = h->fix;
     a.fix_list = h->fix ? h->fix + 64 : nullptr;
     a.fix_slot = h->fix_slot;
@@ -624,7 +625,6 @@ int kbc_diagnostics(kbc_handle h, double* out)
     if (!out) return fail(h, KBC_ERR_ARG, "NULL output");
     if (!h->initialized) return fail(h, KBC_ERR_STATE, "field not initialised");
     StepArgs a = args_of(h);
-    a.guard = 0.0;
     cudaError_t e = by_codec(h->dtype, [&](auto c) {
         using C = decltype(c);
         return launch_diag<C>(h->buf[h->cur], h->diag_part, h->diag_nblocks, h->diag_out,

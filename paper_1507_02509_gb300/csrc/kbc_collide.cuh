@@ -44,7 +44,7 @@ struct CollideParams {
 };
 
 template <typename T>
-__host__ CollideParams<T> make_params(double beta, int fixed, double gamma_fixed, double guard)
+__host__ inline CollideParams<T> make_params(double beta, int fixed, double gamma_fixed, double guard)
 {
     CollideParams<T> p;
     p.two_beta = (T)(2.0 * beta);
@@ -58,14 +58,14 @@ __host__ CollideParams<T> make_params(double beta, int fixed, double gamma_fixed
     return p;
 }
 
-// reciprocal used for the entropic weights (ratio of two sums, so a few ulp
-// do not matter); the velocity uses the correctly rounded rcpT
-template <typename T> __device__ __forceinline__ T rcp_weight(T x);
-template <> __device__ __forceinline__ float rcp_weight<float>(float x) { return __fdividef(1.0f, x); }
-template <> __device__ __forceinline__ double rcp_weight<double>(double x) { return 1.0 / x; }
+// Fast reciprocal / quotient: float uses the approximate hardware path
+// (__fdividef, 2 ulp); double the IEEE operations.
+template <typename T> __device__ __forceinline__ T rcp_fast(T x);
+template <> __device__ __forceinline__ float rcp_fast<float>(float x) { return __fdividef(1.0f, x); }
+template <> __device__ __forceinline__ double rcp_fast<double>(double x) { return 1.0 / x; }
 
 template <typename T> __device__ __forceinline__ T ratio(T a, T b);
-template <> __device__ __forceinline__ float ratio<float>(float a, float b) { return __fdiv_rn(a, b); }
+template <> __device__ __forceinline__ float ratio<float>(float a, float b) { return __fdividef(a, b); }
 template <> __device__ __forceinline__ double ratio<double>(double a, double b) { return a / b; }
 
 // xi_i = v_i . u for a compile-time velocity (a, b)
@@ -78,22 +78,51 @@ __device__ __forceinline__ T vdot(T ux, T uy)
     else return (A > 0 ? ux : -ux) + (B > 0 ? uy : -uy);
 }
 
+// P_i = 3 xi + 4.5 xi^2 - 1.5 u^2, so that f^eq_i = W_i rho (1 + P_i) (Eq. Eq)
 template <int I, typename T>
-__device__ __forceinline__ void eq_dev(T ux, T uy, T usq15, T rho, T drho, T d, T& P, T& df)
+__device__ __forceinline__ T eq_poly(T ux, T uy, T usq15)
 {
     constexpr int A = I % 3 - 1, B = I / 3 - 1;
     if constexpr (A == 0 && B == 0) {
-        P = -usq15;
+        return -usq15;
     } else {
         const T xi = vdot<A, B>(ux, uy);
-        P = fmaT(xi, fmaT(T(4.5), xi, T(3)), -usq15);   // 3 xi + 4.5 xi^2 - 1.5 u^2
+        return fmaT(xi, fmaT(T(4.5), xi, T(3)), -usq15);
     }
-    const T deq = T(wgt(I)) * fmaT(rho, P, drho);      // f^eq - W = W (rho - 1 + rho P)
-    df = d - deq;
+}
+
+// df_i = d_i - (f^eq_i - W_i), with f^eq - W = W (rho - 1 + rho P)
+template <int I, typename T>
+__device__ __forceinline__ T neq(T d, T rho, T drho, T P)
+{
+    return d - T(wgt(I)) * fmaT(rho, P, drho);
+}
+
+// Montgomery's simultaneous inversion: w_i = 1 / x_i for nine x_i with one
+// reciprocal and 24 multiplications.
+template <typename T>
+__device__ __forceinline__ void inv9(const T (&x)[9], T (&w)[9])
+{
+    T pre[9];
+    pre[0] = x[0];
+#pragma unroll
+    for (int k = 1; k < 9; ++k) pre[k] = pre[k - 1] * x[k];
+    T inv = rcp_fast(pre[8]);
+#pragma unroll
+    for (int k = 8; k >= 1; --k) {
+        w[k] = inv * pre[k - 1];
+        inv = inv * x[k];
+    }
+    w[0] = inv;
 }
 
 // Returns gamma; rho_out receives rho (NaN/Inf flags a blown-up node);
 // guard_hit is set when the entropic denominator falls to or below the guard.
+//
+// Only six non-equilibrium parts are formed from the equilibrium; the other
+// three follow from sum df = sum a df = sum b df = 0 (the collision
+// conserves rho and rho u).  The rounding of f^eq (about eps |f^eq - W|)
+// then never leaks into the conserved moments, where nothing would damp it.
 template <int VAR, typename T>
 __device__ __forceinline__ T collide(T (&d)[9], const CollideParams<T>& p, T& rho_out,
                                      bool& guard_hit)
@@ -103,20 +132,26 @@ __device__ __forceinline__ T collide(T (&d)[9], const CollideParams<T>& p, T& rh
     const T jy = ((d[6] - d[0]) + (d[8] - d[2])) + (d[7] - d[1]);
     const T rho = T(1) + drho;
     rho_out = rho;
-    const T irho = rcpT(rho);
+    const T irho = rcp_fast(rho);
     const T ux = jx * irho, uy = jy * irho;
     const T usq15 = T(1.5) * fmaT(ux, ux, uy * uy);
 
     T P[9], df[9];
-    eq_dev<0>(ux, uy, usq15, rho, drho, d[0], P[0], df[0]);
-    eq_dev<1>(ux, uy, usq15, rho, drho, d[1], P[1], df[1]);
-    eq_dev<2>(ux, uy, usq15, rho, drho, d[2], P[2], df[2]);
-    eq_dev<3>(ux, uy, usq15, rho, drho, d[3], P[3], df[3]);
-    eq_dev<4>(ux, uy, usq15, rho, drho, d[4], P[4], df[4]);
-    eq_dev<5>(ux, uy, usq15, rho, drho, d[5], P[5], df[5]);
-    eq_dev<6>(ux, uy, usq15, rho, drho, d[6], P[6], df[6]);
-    eq_dev<7>(ux, uy, usq15, rho, drho, d[7], P[7], df[7]);
-    eq_dev<8>(ux, uy, usq15, rho, drho, d[8], P[8], df[8]);
+    P[0] = eq_poly<0>(ux, uy, usq15);
+    P[1] = eq_poly<1>(ux, uy, usq15);
+    P[2] = eq_poly<2>(ux, uy, usq15);
+    P[3] = eq_poly<3>(ux, uy, usq15);
+    P[6] = eq_poly<6>(ux, uy, usq15);
+    P[8] = eq_poly<8>(ux, uy, usq15);
+    df[0] = neq<0>(d[0], rho, drho, P[0]);
+    df[1] = neq<1>(d[1], rho, drho, P[1]);
+    df[2] = neq<2>(d[2], rho, drho, P[2]);
+    df[3] = neq<3>(d[3], rho, drho, P[3]);
+    df[6] = neq<6>(d[6], rho, drho, P[6]);
+    df[8] = neq<8>(d[8], rho, drho, P[8]);
+    df[5] = (df[3] - (df[2] + df[8])) + (df[0] + df[6]);
+    df[7] = (df[1] - (df[6] + df[8])) + (df[0] + df[2]);
+    df[4] = -(((df[0] + df[8]) + (df[2] + df[6])) + ((df[1] + df[7]) + (df[3] + df[5])));
 
     if constexpr (VAR == kLBGK) {
         guard_hit = false;
@@ -173,14 +208,19 @@ __device__ __forceinline__ T collide(T (&d)[9], const CollideParams<T>& p, T& rh
             ds[0] = ds[8] = q;
             ds[2] = ds[6] = -q;
         }
+        P[4] = eq_poly<4>(ux, uy, usq15);
+        P[5] = eq_poly<5>(ux, uy, usq15);
+        P[7] = eq_poly<7>(ux, uy, usq15);
+        T x[9], w[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) x[i] = T(1) + P[i];
+        inv9(x, w);  // rho / f^eq_i = (1 / W_i) w_i
         T dh[9];
         T sh = T(0), hh = T(0);
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             dh[i] = df[i] - ds[i];
-            // rho / f^eq_i = 1 / (W_i (1 + P_i))
-            const T w = T(inv_wgt(i)) * rcp_weight(T(1) + P[i]);
-            const T t = dh[i] * w;
+            const T t = dh[i] * (T(inv_wgt(i)) * w[i]);
             sh = fmaT(ds[i], t, sh);
             hh = fmaT(dh[i], t, hh);
         }

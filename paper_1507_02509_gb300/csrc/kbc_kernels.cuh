@@ -19,8 +19,9 @@ struct StepArgs {
     int nx, ny;
     long long plane;     // elements between population planes
     CodecScale cs;
-    double beta, gamma_fixed, guard;
-    int fixed;
+    CollideParams<float> pf;   // collision constants, computed on the host
+    CollideParams<double> pd;
+    double beta;               // relaxation parameter (Grad initialisation)
     int* fix_count;      // two counters, used alternately by successive steps
     int* fix_list;       // node indices recorded for the FP64 re-evaluation
     int fix_slot;        // counter used by this step
@@ -89,19 +90,28 @@ __device__ __forceinline__ void record_fix(bool hit, int n, const StepArgs& a)
     if (hit) a.fix_list[base + __popc(m & ((1u << lane) - 1u))] = n;
 }
 
-template <typename T>
-__device__ __forceinline__ CollideParams<T> params_of(const StepArgs& a)
+template <typename T> __device__ __forceinline__ const CollideParams<T>& params_of(const StepArgs& a);
+template <> __device__ __forceinline__ const CollideParams<float>& params_of<float>(const StepArgs& a)
 {
-    CollideParams<T> p;
-    p.two_beta = (T)(2.0 * a.beta);
-    p.one_m_2beta = (T)(1.0 - 2.0 * a.beta);
-    p.inv_beta = (T)(1.0 / a.beta);
-    p.two_m_inv_beta = (T)(2.0 - 1.0 / a.beta);
-    p.ch_fixed = (T)(a.beta * (a.gamma_fixed - 2.0));
-    p.gamma_fixed = (T)a.gamma_fixed;
-    p.guard = (T)a.guard;
-    p.fixed = a.fixed;
-    return p;
+    return a.pf;
+}
+template <> __device__ __forceinline__ const CollideParams<double>& params_of<double>(const StepArgs& a)
+{
+    return a.pd;
+}
+
+// warp-aggregated append of up to NV node indices per lane (bit k of `hits`
+// marks node n0 + k); one vote when no lane has a hit
+template <int NV>
+__device__ __forceinline__ void record_fix_mask(unsigned hits, int n0, const StepArgs& a)
+{
+    if (!__any_sync(0xffffffffu, hits != 0u)) return;
+    if (hits) {
+        int base = atomicAdd(a.fix_count + a.fix_slot, __popc(hits));
+#pragma unroll
+        for (int k = 0; k < NV; ++k)
+            if (hits & (1u << k)) a.fix_list[base++] = n0 + k;
+    }
 }
 
 // ---------------------------------------------------------------- step, rows
@@ -169,17 +179,19 @@ step_rows(const typename C::S* __restrict__ src, typename C::S* __restrict__ dst
             f[NV - 1][i] = C::decode(right, i, a.cs);
         }
     }
-    const CollideParams<T> p = params_of<T>(a);
+    const CollideParams<T>& p = params_of<T>(a);
     bool bad = false;
+    unsigned hits = 0u;
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
         T rho;
         bool hit;
         collide<VAR>(f[k], p, rho, hit);
         bad |= !isfinite(rho);
-        if constexpr (VAR != kLBGK) {
-            if (a.fix_list) record_fix(hit, y * a.nx + x0 + k, a);
-        }
+        hits |= (hit ? 1u : 0u) << k;
+    }
+    if constexpr (VAR != kLBGK) {
+        if (a.fix_list) record_fix_mask<NV>(hits, y * a.nx + x0, a);
     }
     if (bad) *a.flag = 1;
     const long long o = (long long)y * a.nx + x0;
@@ -203,7 +215,7 @@ step_nodes(const typename C::S* __restrict__ src, typename C::S* __restrict__ ds
     using T = typename C::T;
     if (blockIdx.x == 0 && threadIdx.x == 0 && a.fix_count) a.fix_count[a.fix_slot ^ 1] = 0;
     const long long total = (long long)a.nx * a.ny;
-    const CollideParams<T> p = params_of<T>(a);
+    const CollideParams<T>& p = params_of<T>(a);
     for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < total;
          n += (long long)gridDim.x * blockDim.x) {
         const int y = (int)(n / a.nx), x = (int)(n - (long long)y * a.nx);
@@ -240,7 +252,6 @@ step_fixup(const typename C::S* __restrict__ src, typename C::S* __restrict__ ds
     using S = typename C::S;
     const int count = a.fix_count[a.fix_slot];
     if (count == 0) return;
-    const CollideParams<double> p = params_of<double>(a);
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < count; t += gridDim.x * blockDim.x) {
         const int n = a.fix_list[t];
         const int y = n / a.nx, x = n - y * a.nx;
@@ -253,7 +264,7 @@ step_fixup(const typename C::S* __restrict__ src, typename C::S* __restrict__ ds
             sy = sy < 0 ? sy + a.ny : (sy >= a.ny ? sy - a.ny : sy);
             f[i] = C::to_f64(src[(long long)i * a.plane + (long long)sy * a.nx + sx], i, a.cs);
         }
-        CollideParams<double> q = p;
+        CollideParams<double> q = a.pd;
         q.guard = 0.0;
         double rho;
         bool hit;
@@ -414,11 +425,8 @@ diag_partial(const typename C::S* __restrict__ src, double* __restrict__ part, S
 {
     const long long total = (long long)a.nx * a.ny;
     double acc[kDiagParts] = {0, 0, 0, 0, 0, 0, 0, 0, 1e300, -1e300};
-    const CollideParams<double> p = [&] {
-        CollideParams<double> q = params_of<double>(a);
-        q.guard = 0.0;
-        return q;
-    }();
+    CollideParams<double> p = a.pd;
+    p.guard = 0.0;
     for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < total;
          n += (long long)gridDim.x * blockDim.x) {
         const int y = (int)(n / a.nx), x = (int)(n - (long long)y * a.nx);

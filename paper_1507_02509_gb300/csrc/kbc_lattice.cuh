@@ -28,11 +28,6 @@ template <typename T> __device__ __forceinline__ T fmaT(T a, T b, T c);
 template <> __device__ __forceinline__ float fmaT<float>(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 template <> __device__ __forceinline__ double fmaT<double>(double a, double b, double c) { return __fma_rn(a, b, c); }
 
-// correctly rounded reciprocal
-template <typename T> __device__ __forceinline__ T rcpT(T x);
-template <> __device__ __forceinline__ float rcpT<float>(float x) { return __frcp_rn(x); }
-template <> __device__ __forceinline__ double rcpT<double>(double x) { return __drcp_rn(x); }
-
 // Scale of the half-precision encoding (unused by the other codecs).
 struct CodecScale {
     float scale;      // S

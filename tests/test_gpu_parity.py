@@ -2,8 +2,12 @@
 
 All inputs are seeded; the oracle always starts from the same (storage-
 representable) populations as the GPU.  Tolerances:
-  f64: populations within 1e-13 absolute after one step, 1e-12 relative
-       velocity after 1000 steps;
+  f64: populations within 1e-13 absolute after one step; after many steps
+       the relative velocity error stays below max(1e-12, 3 x the oracle's
+       own rounding-sensitivity floor), the gap between the oracle and the
+       oracle started from 1-ulp-perturbed populations (KBC amplifies
+       rounding through gamma: about 4e-12 for A and B after 1000 steps of
+       the 64^2 vortex, 5e-14 for LBGK);
   f32: 2e-6 absolute per population after one step (a few float ulps of
        f ~ 0.44 plus the float evaluation of the entropic weights), 1e-5
        relative velocity after 1000 laminar steps;
@@ -18,8 +22,8 @@ torch = pytest.importorskip("torch")
 
 import oracle as O  # noqa: E402
 from paper_1507_02509_gb300 import KBCError, Lattice, capi, flows  # noqa: E402
-from tests.gpu_helpers import (max_rel_velocity_error, random_field, representable,  # noqa: E402
-                               weights, windows)
+from tests.gpu_helpers import (max_rel_velocity_error, oracle_sensitivity,  # noqa: E402
+                               random_field, representable, weights, windows)
 
 pytestmark = pytest.mark.gpu
 
@@ -106,11 +110,17 @@ def test_taylor_green_1000_steps(variant, dtype):
     r, vx, vy = (t.cpu().numpy() for t in lat.moments())
     lat.sync()
     lat.close()
-    ref = O.step(O.init_feq(rho, ux, uy), OV[variant], beta, 1000, nthreads=8)
+    g0 = O.init_feq(rho, ux, uy)
+    ref = O.step(g0, OV[variant], beta, 1000, nthreads=8)
     _, rx, ry = O.macro(ref)
     err = max_rel_velocity_error((vx, vy), (rx, ry))
-    tol = 1e-12 if dtype == "f64" else 1e-5
-    assert err < tol, err
+    if dtype == "f64":
+        floor = oracle_sensitivity(g0, OV[variant], beta, 1000, nthreads=8, ref_uv=(rx, ry))
+        tol = max(1e-12, 3.0 * floor)
+    else:
+        tol = 1e-5
+    print(f"TG {variant} {dtype}: max rel velocity error {err:.3e} (tol {tol:.1e})")
+    assert err < tol, (err, tol)
     # and the vortex decays at the rate set by Eq. viscosity (2% at 64^2)
     k = 2 * math.pi / n
     amp = np.sum(vx * ux) / np.sum(ux * ux)
@@ -129,17 +139,25 @@ def test_shear_layer_1024(dtype):
     lat = Lattice(n, n, variant="B", beta=beta, dtype=dtype)
     lat.init(rho, ux, uy)
     g = O.init_feq(rho, ux, uy)
+    rng = np.random.default_rng(0)
+    gp = g * (1.0 + np.finfo(np.float64).eps * rng.choice([-1.0, 0.0, 1.0], size=g.shape))
     done = 0
-    for target, tol in ((100, 1e-12 if dtype == "f64" else 1e-5),
-                        (1000, 1e-11 if dtype == "f64" else 1e-4)):
+    for target, f32_tol in ((100, 1e-5), (1000, 1e-4)):
         lat.step(target - done)
         g = O.step(g, O.B, beta, target - done, nthreads=16)
+        if dtype == "f64":
+            gp = O.step(gp, O.B, beta, target - done, nthreads=16)
         done = target
         _, vx, vy = (t.cpu().numpy() for t in lat.moments())
         _, rx, ry = O.macro(g)
         err = max_rel_velocity_error((vx, vy), (rx, ry))
-        print(f"shear layer {dtype} step {target}: max rel velocity error {err:.3e}")
-        assert err < tol, (target, err)
+        if dtype == "f64":
+            _, px, py = O.macro(gp)
+            tol = max(1e-12, 3.0 * max_rel_velocity_error((px, py), (rx, ry)))
+        else:
+            tol = f32_tol
+        print(f"shear layer {dtype} step {target}: max rel velocity error {err:.3e} (tol {tol:.1e})")
+        assert err < tol, (target, err, tol)
     lat.close()
 
 
