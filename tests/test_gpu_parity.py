@@ -283,7 +283,9 @@ def test_grad_initialisation_matches_oracle(dtype):
     got = lat.populations().cpu().numpy()
     lat.close()
     ref = representable(O.init_grad(beta, rho, ux, uy), dtype)
-    assert np.max(np.abs(got - ref)) < (1e-16 if dtype == "f64" else 1e-9)
+    # a few ulps of f ~ 0.44 (ulp 5.6e-17): the two sides order the sums of
+    # Eq. Grad differently
+    assert np.max(np.abs(got - ref)) < (3e-16 if dtype == "f64" else 1e-9)
 
 
 def test_guard_pass_recomputes_in_fp64():
