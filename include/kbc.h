@@ -168,6 +168,33 @@ int kbc_moments(kbc_handle h, double* rho, double* u);
  *   [8] spatial std of |u|^2/2   [9] spatial std of w^2/2 */
 int kbc_diagnostics(kbc_handle h, double* out);
 
+/* Diagnostics of a caller-owned population field without any device
+ * allocation.  The paper has no counterpart to this call.
+ *
+ * For callers that cannot allocate device memory: code whose device memory
+ * is fully owned by another allocator (a framework's caching pool, a fixed
+ * arena sized at start-up), and code that must not trigger the implicit
+ * device-wide synchronisation of cudaMalloc/cudaFree inside a timed loop.
+ * It needs no handle: f is the caller's FP64 population field
+ * f[9][ny][nx] in DEVICE memory (a host pointer gives KBC_ERR_ARG, since
+ * staging it would need an allocation); out (host or device) receives the
+ * KBC_DIAG_N values documented at kbc_diagnostics, for the given variant
+ * and beta with the entropic gamma.  Work runs on `stream` (a cudaStream_t,
+ * NULL = legacy default) and the call waits for it (bounded,
+ * KBC_ERR_TIMEOUT).
+ *
+ * Scratch: a file-scope device array of about 1.3 MB that every GPU that
+ * loads the library holds until the process exits; it bounds the grid to
+ * nx * ny <= 2^28 nodes (e.g. 16384 x 16384); larger grids give
+ * KBC_ERR_ARG.  The first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  All calls share the array, so calls that
+ * overlap on the GPU (different streams or threads) race and must be
+ * serialised by the caller.  Nothing in the array needs clearing: every
+ * call overwrites the parts it reads. */
+int kbc_diagnostics_noalloc(int nx, int ny, int variant, double beta, const double* f,
+                            double* out, void* stream);
+
 /* Bytes of population traffic per lattice-node update of this handle's
  * storage (9 reads + 9 writes), for roofline accounting. */
 int kbc_bytes_per_update(kbc_handle h, double* bytes);

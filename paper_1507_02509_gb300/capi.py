@@ -51,6 +51,7 @@ SIGNATURES = {
     "kbc_probe": (_i, [_vp, _i, _vp, _vp]),
     "kbc_moments": (_i, [_vp, _vp, _vp]),
     "kbc_diagnostics": (_i, [_vp, _vp]),
+    "kbc_diagnostics_noalloc": (_i, [_i, _i, _i, _d, _vp, _vp, _vp]),
     "kbc_bytes_per_update": (_i, [_vp, ctypes.POINTER(_d)]),
     "kbc_last_error": (ctypes.c_char_p, [_vp]),
 }
@@ -181,6 +182,16 @@ def kbc_moments(h, rho, u):
 
 def kbc_diagnostics(h, out):
     return check(h, load().kbc_diagnostics(h, ptr(out)))
+
+
+def kbc_diagnostics_noalloc(nx: int, ny: int, variant: int, beta: float, f, out,
+                            stream=None):
+    """Diagnostics of a caller-owned FP64 device field, no device allocation."""
+    st = load().kbc_diagnostics_noalloc(int(nx), int(ny), int(variant), float(beta), ptr(f),
+                                        ptr(out), stream)
+    if st != KBC_OK:
+        raise KBCError(st, "kbc_diagnostics_noalloc failed")
+    return st
 
 
 def kbc_bytes_per_update(h) -> float:
