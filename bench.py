@@ -62,13 +62,16 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
+STEP_KERNEL_SOURCES = ("kbc_lattice.cuh", "kbc_collide.cuh", "kbc_kernels.cuh", "kbc_launch.cuh")
+
+
 def kernel_source_hash() -> str:
+    """Hash of the sources that define the step kernel and its launch."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1507_02509_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh")):
-            with open(os.path.join(csrc, name), "rb") as f:
-                h.update(name.encode() + f.read())
+    for name in STEP_KERNEL_SOURCES:
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode() + f.read())
     return h.hexdigest()[:16]
 
 
@@ -252,7 +255,7 @@ def run_ours(args):
         lat.set_guard(0.0)
     t_roof = time_steps(lat, k_roof, stream)
     if guard_on:
-        lat.set_guard(1e-15)
+        lat.set_guard(1e-16)
     kernel_s = t_roof / k_roof
     peak, peak_kind = load_peaks()
     achieved = bpu * n * n / kernel_s / 1e9

@@ -113,7 +113,7 @@ int kbc_set_gamma_mode(kbc_handle h, int mode, double gamma_fixed);
 /* Threshold on <dh|dh> (entropic scalar product of Sec. 4, computed with the
  * weights rho/f^eq_i) below which an F32/F16 node is recomputed entirely in
  * FP64 from its stored populations by a second pass.  0 disables the pass.
- * Defaults: 1e-15 for F32 (about 30x the float rounding level of that sum
+ * Defaults: 1e-16 for F32 (about 10x the float rounding level of that sum
  * for |u| ~ 0.03), 0 for F16; F64 ignores it. */
 int kbc_set_guard(kbc_handle h, double threshold);
 

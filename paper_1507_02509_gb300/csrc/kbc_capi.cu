@@ -317,7 +317,7 @@ int kbc_create(int nx, int ny, int variant, double beta, int dtype, kbc_handle* 
     h->beta = beta;
     h->dtype = dtype;
     h->elem = elem_size(dtype);
-    h->guard = (dtype == KBC_F32_DEV) ? 1e-15 : 0.0;
+    h->guard = (dtype == KBC_F32_DEV) ? 1e-16 : 0.0;
     cudaError_t e = cudaGetDevice(&h->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
     if (e != cudaSuccess) {
