@@ -195,6 +195,28 @@ int kbc_diagnostics(kbc_handle h, double* out);
 int kbc_diagnostics_noalloc(int nx, int ny, int variant, double beta, const double* f,
                             double* out, void* stream);
 
+/* Discrete adjoint (not in the paper): J and its gradients for
+ *   g^0 = f^eq(rho0, u0) (Eq. Eq), g^{n+1} = one step of kbc_step applied to g^n,
+ *   objective 0: J = sum_x rho |u|^2 / 2 of g^nsteps (kinetic energy),
+ *   objective 1: J = sum_x |u - u_target|^2 / 2 of g^nsteps (misfit).
+ * The reverse sweep applies lambda^n = P^T (dC/df)^T lambda^{n+1} with the
+ * hand-written derivative of the collision, including the dependence of
+ * gamma* (Eq. result21) on f and beta; dJ/dbeta sums lambda^{n+1} . dC/dbeta.
+ * Forward states are checkpointed every ckpt_every steps and each segment
+ * is recomputed during the reverse sweep (bit-identical to the forward).
+ *   rho0 [ny][nx], u0 [2][ny][nx], u_target [2][ny][nx] (objective 1 only,
+ *   else NULL): host or device.  J, grad_beta: host doubles.  grad_u0
+ *   [2][ny][nx]: host or device.  Adjoint fields are held in the arithmetic
+ *   type of the storage (double for F64, float for F32/F16).
+ * Device memory for the call, from the handle's allocator and released
+ * before returning: ceil(nsteps/ckpt_every) + ckpt_every + 1 population
+ * fields, two adjoint fields and O(nx ny) doubles.  Synchronises the
+ * stream.  Afterwards the handle holds g^nsteps.  Errors: KBC_ERR_ARG,
+ * KBC_ERR_NOMEM, KBC_ERR_NONFINITE (the forward sweep blew up). */
+int kbc_adjoint(kbc_handle h, const double* rho0, const double* u0, int nsteps, int ckpt_every,
+                int objective, const double* u_target, double* J, double* grad_u0,
+                double* grad_beta);
+
 /* Bytes of population traffic per lattice-node update of this handle's
  * storage (9 reads + 9 writes), for roofline accounting. */
 int kbc_bytes_per_update(kbc_handle h, double* bytes);

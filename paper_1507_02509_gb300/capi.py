@@ -52,6 +52,8 @@ SIGNATURES = {
     "kbc_moments": (_i, [_vp, _vp, _vp]),
     "kbc_diagnostics": (_i, [_vp, _vp]),
     "kbc_diagnostics_noalloc": (_i, [_i, _i, _i, _d, _vp, _vp, _vp]),
+    "kbc_adjoint": (_i, [_vp, _vp, _vp, _i, _i, _i, _vp, ctypes.POINTER(_d), _vp,
+                         ctypes.POINTER(_d)]),
     "kbc_bytes_per_update": (_i, [_vp, ctypes.POINTER(_d)]),
     "kbc_last_error": (ctypes.c_char_p, [_vp]),
 }
@@ -192,6 +194,17 @@ def kbc_diagnostics_noalloc(nx: int, ny: int, variant: int, beta: float, f, out,
     if st != KBC_OK:
         raise KBCError(st, "kbc_diagnostics_noalloc failed")
     return st
+
+
+def kbc_adjoint(h, rho0, u0, nsteps: int, ckpt_every: int, objective: int, u_target,
+                grad_u0):
+    """Returns (J, dJ/dbeta); dJ/du0 is written into grad_u0 [2][ny][nx]."""
+    J = ctypes.c_double()
+    gb = ctypes.c_double()
+    check(h, load().kbc_adjoint(h, ptr(rho0), ptr(u0), int(nsteps), int(ckpt_every),
+                                int(objective), ptr(u_target), ctypes.byref(J), ptr(grad_u0),
+                                ctypes.byref(gb)))
+    return J.value, gb.value
 
 
 def kbc_bytes_per_update(h) -> float:

@@ -1,0 +1,299 @@
+// Discrete adjoint of the stream-collide step (not part of the paper; it
+// gives gradients of an objective of the final field with respect to the
+// initial velocity and beta).
+//
+// Forward map of one step: g^{n+1} = C(P g^n), P the periodic pull
+// f_i(x) = g_i(x - v_i), C the per-node collision of kbc_collide.cuh.
+// Reverse: lambda^n = P^T (dC/df)^T lambda^{n+1}, where P^T sends the
+// adjoint of the population pulled from x - v_i back there, and
+// dJ/dbeta = sum_n sum_x lambda^{n+1}(x) . dC/dbeta.
+//
+// collide_adjoint() is the hand-written reverse mode of collide(): it
+// recomputes the forward quantities and propagates lambda back through the
+// update f' = f - 2 beta df - beta (gamma - 2) dh, the entropic products and
+// gamma* (Eq. result21, including the dependence of gamma on f), the split
+// (Table 1 bases, with the velocity dependence of the central basis), the
+// equilibrium (Eq. Eq) and the moments.  It differentiates the exact map:
+// all nine non-equilibrium parts are taken from the equilibrium (the
+// forward kernel derives three of them from conservation, which is the same
+// function).
+#pragma once
+
+#include "kbc_kernels.cuh"
+
+namespace kbc {
+
+template <int VAR, typename T>
+__device__ __forceinline__ void collide_adjoint(const T (&d)[9], const T (&lam)[9],
+                                                const CollideParams<T>& p, T (&mu)[9],
+                                                T& beta_bar)
+{
+    constexpr bool central = (VAR == kA || VAR == kB);
+    const T two_beta = p.two_beta;
+    const T beta = T(0.5) * two_beta;
+    // ---------------------------------------------------------------- forward
+    const T drho = ((d[0] + d[8]) + (d[2] + d[6])) + ((d[1] + d[7]) + (d[3] + d[5])) + d[4];
+    const T jx = ((d[2] - d[0]) + (d[8] - d[6])) + (d[5] - d[3]);
+    const T jy = ((d[6] - d[0]) + (d[8] - d[2])) + (d[7] - d[1]);
+    const T rho = T(1) + drho;
+    const T irho = T(1) / rho;
+    const T ux = jx * irho, uy = jy * irho;
+    const T usq15 = T(1.5) * (ux * ux + uy * uy);
+    T xi[9], P[9], df[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        xi[i] = T(va(i)) * ux + T(vb(i)) * uy;
+        P[i] = xi[i] * (T(3) + T(4.5) * xi[i]) - usq15;
+        df[i] = d[i] - T(wgt(i)) * (drho + rho * P[i]);
+    }
+    T dfb[9], Pb[9];
+    T uxb = T(0), uyb = T(0);
+    T bb = T(0);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        dfb[i] = -two_beta * lam[i];
+        Pb[i] = T(0);
+        bb -= T(2) * lam[i] * df[i];
+    }
+    if constexpr (VAR != kLBGK) {
+        const T corner = (df[0] + df[2]) + (df[6] + df[8]);
+        const T m20 = corner + (df[3] + df[5]);
+        const T m02 = corner + (df[1] + df[7]);
+        const T m11 = (df[0] + df[8]) - (df[2] + df[6]);
+        T c20, c02;
+        if constexpr (VAR == kA || VAR == kC) {
+            c20 = m20;
+            c02 = m02;
+        } else {
+            c20 = T(0.5) * (m20 - m02);
+            c02 = -c20;
+        }
+        const T cx = central ? ux : T(0), cy = central ? uy : T(0);
+        const T e0x[3] = {T(0.5) * cx * (cx - T(1)), T(1) - cx * cx, T(0.5) * cx * (cx + T(1))};
+        const T e0y[3] = {T(0.5) * cy * (cy - T(1)), T(1) - cy * cy, T(0.5) * cy * (cy + T(1))};
+        const T e1x[3] = {cx - T(0.5), T(-2) * cx, cx + T(0.5)};
+        const T e1y[3] = {cy - T(0.5), T(-2) * cy, cy + T(0.5)};
+        const T e2[3] = {T(0.5), T(-1), T(0.5)};
+        T ds[9], dh[9], x[9], q[9];
+        T sh = T(0), hh = T(0);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const int a = i % 3, b = i / 3;
+            ds[i] = c20 * e2[a] * e0y[b] + c02 * e0x[a] * e2[b] + m11 * e1x[a] * e1y[b];
+            dh[i] = df[i] - ds[i];
+            x[i] = T(1) + P[i];
+            q[i] = T(inv_wgt(i)) / x[i];
+            sh += ds[i] * dh[i] * q[i];
+            hh += dh[i] * dh[i] * q[i];
+        }
+        T ch, R = T(0);
+        const bool has_h = hh > T(0);
+        if (p.fixed) {
+            ch = p.ch_fixed;
+        } else if (has_h) {
+            R = sh / hh;
+            ch = p.one_m_2beta * (T(1) + R);
+        } else {
+            ch = T(0);
+        }
+        // ---------------------------------------------------------- reverse
+        T dhb[9], dsb[9];
+        T chb = T(0);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            dhb[i] = -ch * lam[i];
+            chb -= lam[i] * dh[i];
+        }
+        T Rb = T(0);
+        if (p.fixed) {
+            bb += chb * (p.gamma_fixed - T(2));
+        } else if (has_h) {
+            bb += chb * (T(-2) * (T(1) + R));
+            Rb = chb * p.one_m_2beta;
+        }
+        const T shb = has_h ? Rb / hh : T(0);
+        const T hhb = has_h ? -Rb * R / hh : T(0);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            dsb[i] = shb * dh[i] * q[i];
+            dhb[i] += shb * ds[i] * q[i] + T(2) * hhb * dh[i] * q[i];
+            const T qb = shb * ds[i] * dh[i] + hhb * dh[i] * dh[i];
+            Pb[i] -= qb * q[i] / x[i];
+            dfb[i] += dhb[i];
+            dsb[i] -= dhb[i];
+        }
+        T c20b = T(0), c02b = T(0), m11b = T(0);
+        T e0xb[3] = {T(0), T(0), T(0)}, e0yb[3] = {T(0), T(0), T(0)};
+        T e1xb[3] = {T(0), T(0), T(0)}, e1yb[3] = {T(0), T(0), T(0)};
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const int a = i % 3, b = i / 3;
+            c20b += dsb[i] * e2[a] * e0y[b];
+            c02b += dsb[i] * e0x[a] * e2[b];
+            m11b += dsb[i] * e1x[a] * e1y[b];
+            e0yb[b] += dsb[i] * c20 * e2[a];
+            e0xb[a] += dsb[i] * c02 * e2[b];
+            e1xb[a] += dsb[i] * m11 * e1y[b];
+            e1yb[b] += dsb[i] * m11 * e1x[a];
+        }
+        if constexpr (central) {
+            // d e0(c)/dc = e1(c), d e1(c)/dc = (1, -2, 1)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                uxb += e0xb[k] * e1x[k] + e1xb[k] * (k == 1 ? T(-2) : T(1));
+                uyb += e0yb[k] * e1y[k] + e1yb[k] * (k == 1 ? T(-2) : T(1));
+            }
+        }
+        T m20b, m02b;
+        if constexpr (VAR == kA || VAR == kC) {
+            m20b = c20b;
+            m02b = c02b;
+        } else {
+            m20b = T(0.5) * (c20b - c02b);
+            m02b = -m20b;
+        }
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const T a = T(va(i)), b = T(vb(i));
+            dfb[i] += a * a * m20b + b * b * m02b + a * b * m11b;
+        }
+    }
+    // ------------------------------------------------- equilibrium and moments
+    T drhob = T(0), usqb = T(0);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        mu[i] = lam[i] + dfb[i];
+        drhob -= dfb[i] * T(wgt(i)) * (T(1) + P[i]);
+        Pb[i] -= dfb[i] * T(wgt(i)) * rho;
+        usqb -= Pb[i];
+        const T xib = Pb[i] * (T(3) + T(9) * xi[i]);
+        uxb += T(va(i)) * xib;
+        uyb += T(vb(i)) * xib;
+    }
+    uxb += T(3) * ux * usqb;
+    uyb += T(3) * uy * usqb;
+    const T jxb = uxb * irho, jyb = uyb * irho;
+    const T irhob = uxb * jx + uyb * jy;
+    drhob -= irhob * irho * irho;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) mu[i] += drhob + T(va(i)) * jxb + T(vb(i)) * jyb;
+    (void)beta;
+    beta_bar = bb;
+}
+
+// block-wide FP64 sum of v, added by thread 0 to *acc (fixed order)
+__device__ __forceinline__ void block_add(double v, double* acc)
+{
+    __shared__ double sm[256];
+    sm[threadIdx.x] = v;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sm[threadIdx.x] += sm[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *acc += sm[0];
+}
+
+// lambda^n from lambda^{n+1} and the forward state g^n; beta adjoint summed
+// into part[blockIdx.x] (same grid every step, so the sum order is fixed).
+template <int VAR, class C>
+__global__ void __launch_bounds__(256)
+adj_step(const typename C::S* __restrict__ g, const typename C::T* __restrict__ lam_in,
+         typename C::T* __restrict__ lam_out, double* __restrict__ part, StepArgs a)
+{
+    using T = typename C::T;
+    const CollideParams<T>& p = params_of<T>(a);
+    const long long total = (long long)a.nx * a.ny;
+    double bsum = 0.0;
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < total;
+         n += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(n / a.nx), x = (int)(n - (long long)y * a.nx);
+        T d[9], lam[9], mu[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const int ai = i % 3 - 1, bi = i / 3 - 1;
+            int sx = x - ai, sy = y - bi;
+            sx = sx < 0 ? sx + a.nx : (sx >= a.nx ? sx - a.nx : sx);
+            sy = sy < 0 ? sy + a.ny : (sy >= a.ny ? sy - a.ny : sy);
+            const long long src = (long long)sy * a.nx + sx;
+            d[i] = C::decode(g[(long long)i * a.plane + src], i, a.cs);
+            lam[i] = lam_in[(long long)i * a.plane + n];
+        }
+        T bbar;
+        collide_adjoint<VAR>(d, lam, p, mu, bbar);
+        bsum += (double)bbar;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const int ai = i % 3 - 1, bi = i / 3 - 1;
+            int sx = x - ai, sy = y - bi;
+            sx = sx < 0 ? sx + a.nx : (sx >= a.nx ? sx - a.nx : sx);
+            sy = sy < 0 ? sy + a.ny : (sy >= a.ny ? sy - a.ny : sy);
+            lam_out[(long long)i * a.plane + (long long)sy * a.nx + sx] = mu[i];
+        }
+    }
+    block_add(bsum, part + blockIdx.x);
+}
+
+// J of the final field and lambda^N = dJ/dg^N.  objective 0: kinetic energy
+// sum_x rho |u|^2 / 2; objective 1: misfit sum_x |u - u_target|^2 / 2.
+template <class C>
+__global__ void __launch_bounds__(256)
+adj_objective(const typename C::S* __restrict__ g, const double* __restrict__ tx,
+              const double* __restrict__ ty, int objective, typename C::T* __restrict__ lam,
+              double* __restrict__ part, StepArgs a)
+{
+    using T = typename C::T;
+    const long long total = (long long)a.nx * a.ny;
+    double jsum = 0.0;
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < total;
+         n += (long long)gridDim.x * blockDim.x) {
+        double r, ux, uy;
+        node_macro<C>(g, n, a, r, ux, uy);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const double vx = va(i), vy = vb(i);
+            double l;
+            if (objective == 0) {
+                l = vx * ux + vy * uy - 0.5 * (ux * ux + uy * uy);
+            } else {
+                l = ((ux - tx[n]) * (vx - ux) + (uy - ty[n]) * (vy - uy)) / r;
+            }
+            lam[(long long)i * a.plane + n] = (T)l;
+        }
+        if (objective == 0)
+            jsum += 0.5 * r * (ux * ux + uy * uy);
+        else
+            jsum += 0.5 * ((ux - tx[n]) * (ux - tx[n]) + (uy - ty[n]) * (uy - ty[n]));
+    }
+    block_add(jsum, part + blockIdx.x);
+}
+
+// dJ/du0 = (d f^eq / du)^T lambda^0 for the equilibrium initialisation.
+template <class C>
+__global__ void __launch_bounds__(256)
+adj_grad_u0(const double* __restrict__ rho0, const double* __restrict__ ux0,
+            const double* __restrict__ uy0, const typename C::T* __restrict__ lam,
+            double* __restrict__ gx, double* __restrict__ gy, StepArgs a)
+{
+    const long long total = (long long)a.nx * a.ny;
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < total;
+         n += (long long)gridDim.x * blockDim.x) {
+        const double r = rho0[n], x = ux0[n], y = uy0[n];
+        double sx = 0.0, sy = 0.0;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const double vx = va(i), vy = vb(i);
+            const double xi = vx * x + vy * y;
+            const double l = (double)lam[(long long)i * a.plane + n];
+            // f^eq_i = W_i rho (1 + 3 xi + 4.5 xi^2 - 1.5 u^2)
+            sx += l * wgt(i) * r * (3.0 * vx + 9.0 * xi * vx - 3.0 * x);
+            sy += l * wgt(i) * r * (3.0 * vy + 9.0 * xi * vy - 3.0 * y);
+        }
+        gx[n] = sx;
+        gy[n] = sy;
+    }
+}
+
+__global__ void sum_partials(const double* __restrict__ part, int n, double* __restrict__ out);
+
+}  // namespace kbc

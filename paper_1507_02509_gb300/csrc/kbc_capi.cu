@@ -8,6 +8,7 @@
 #include <new>
 #include <string>
 #include <thread>
+#include <vector>
 
 #include "../../include/kbc.h"
 #include "kbc_launch.cuh"
@@ -52,6 +53,20 @@ __global__ void diag_final(const double* __restrict__ part, int nblocks, double*
         out[8] = sqrt(fmax(sm[4][0] * inv - e * e, 0.0));
         out[9] = sqrt(fmax(sm[6][0] * inv - z * z, 0.0));
     }
+}
+
+__global__ void sum_partials(const double* __restrict__ part, int n, double* __restrict__ out)
+{
+    __shared__ double sm[256];
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < n; b += blockDim.x) acc += part[b];
+    sm[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sm[threadIdx.x] += sm[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = sm[0];
 }
 
 }  // namespace kbc
@@ -218,6 +233,51 @@ int check_h(kbc_ctx* h)
 }
 
 }  // namespace
+
+// One step from src to dst with the handle's settings (guard pass and its
+// alternating counters included).
+static int step_into(kbc_handle h, const void* src, void* dst)
+{
+    Launch L;
+    L.variant = h->variant;
+    L.rows = (h->nx % (32 * vec_width(h->dtype))) == 0;
+    L.stream = h->stream;
+    L.num_sms = h->num_sms;
+    const bool guard_on = h->dtype != KBC_F64 && h->variant != KBC_LBGK &&
+                          h->gamma_mode == KBC_GAMMA_ENTROPIC && h->guard > 0.0 && h->fix;
+    L.fixup = guard_on;
+    L.src = src;
+    L.dst = dst;
+    L.a = args_of(h);
+    if (!guard_on) L.a.fix_list = nullptr;
+    cudaError_t e = by_codec(h->dtype, [&](auto c) {
+        using C = decltype(c);
+        return launch_step<C>(L);
+    });
+    if (e != cudaSuccess) return cuda_fail(h, e, "step launch");
+    if (guard_on) h->fix_slot ^= 1;
+    return KBC_OK;
+}
+
+// device buffers owned by one call, released on every exit path
+struct CallBuffers {
+    kbc_ctx* h;
+    void* p[64];
+    int n = 0;
+    explicit CallBuffers(kbc_ctx* hh) : h(hh) {}
+    void* get(size_t bytes)
+    {
+        if (n >= 64) return nullptr;
+        void* q = dev_alloc(h, bytes);
+        if (q) p[n++] = q;
+        return q;
+    }
+    ~CallBuffers()
+    {
+        cudaStreamSynchronize(h->stream);
+        for (int i = n - 1; i >= 0; --i) dev_free(h, p[i]);
+    }
+};
 
 static int init_common(kbc_handle h, const double* rho, const double* u, bool grad)
 {
@@ -492,28 +552,10 @@ int kbc_step(kbc_handle h, int nsteps)
     if (!h->initialized) return fail(h, KBC_ERR_STATE, "field not initialised");
     if (*h->flag_host) return fail(h, KBC_ERR_NONFINITE, "non-finite populations detected");
     if (nsteps == 0) return KBC_OK;
-    Launch L;
-    L.variant = h->variant;
-    L.rows = (h->nx % (32 * vec_width(h->dtype))) == 0;
-    L.stream = h->stream;
-    L.num_sms = h->num_sms;
-    const bool guard_on = h->dtype != KBC_F64 && h->variant != KBC_LBGK &&
-                          h->gamma_mode == KBC_GAMMA_ENTROPIC && h->guard > 0.0 && h->fix;
-    L.fixup = guard_on;
     for (int s = 0; s < nsteps; ++s) {
-        L.src = h->buf[h->cur];
-        L.dst = h->buf[h->cur ^ 1];
-        L.a = args_of(h);
-        if (!guard_on) {
-            L.a.fix_list = nullptr;
-        }
-        cudaError_t e = by_codec(h->dtype, [&](auto c) {
-            using C = decltype(c);
-            return launch_step<C>(L);
-        });
-        if (e != cudaSuccess) return cuda_fail(h, e, "step launch");
+        rc = step_into(h, h->buf[h->cur], h->buf[h->cur ^ 1]);
+        if (rc) return rc;
         h->cur ^= 1;
-        if (guard_on) h->fix_slot ^= 1;
     }
     cudaError_t e = cudaMemcpyAsync(h->flag_host, h->flag_dev, sizeof(int), cudaMemcpyDeviceToHost,
                                     h->stream);
@@ -634,6 +676,129 @@ int kbc_diagnostics(kbc_handle h, double* out)
     e = cudaMemcpyAsync(out, h->diag_out, KBC_DIAG_N * sizeof(double), cudaMemcpyDefault, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "diagnostics copy");
     return wait_stream(h, 0);
+}
+
+int kbc_adjoint(kbc_handle h, const double* rho0, const double* u0, int nsteps, int ckpt_every,
+                int objective, const double* u_target, double* J, double* grad_u0,
+                double* grad_beta)
+{
+    int rc = check_h(h);
+    if (rc) return rc;
+    if (!rho0 || !u0 || !J || !grad_u0 || !grad_beta) return fail(h, KBC_ERR_ARG, "NULL argument");
+    if (nsteps < 0 || ckpt_every < 1) return fail(h, KBC_ERR_ARG, "nsteps >= 0, ckpt_every >= 1");
+    if (objective != 0 && objective != 1) return fail(h, KBC_ERR_ARG, "objective must be 0 or 1");
+    if (objective == 1 && !u_target) return fail(h, KBC_ERR_ARG, "objective 1 needs u_target");
+    const long long n = (long long)h->nx * h->ny;
+    const size_t field = (size_t)9 * h->plane * h->elem;
+    const size_t tsize = (h->dtype == KBC_F64) ? sizeof(double) : sizeof(float);
+    const size_t lamf = (size_t)9 * h->plane * tsize;
+    const int K = ckpt_every;
+    const int nseg = (nsteps + K - 1) / K;
+    const int seglen = nsteps < K ? nsteps : K;
+    const int nb = adj_blocks(n, h->num_sms);
+    CallBuffers B(h);
+    // inputs on the device: rho0, u0 (and the target)
+    double* in = static_cast<double*>(B.get((size_t)(objective == 1 ? 5 : 3) * n * sizeof(double)));
+    double* gdev = static_cast<double*>(B.get((size_t)2 * n * sizeof(double)));
+    double* part = static_cast<double*>(B.get((size_t)(2 * nb + 8) * sizeof(double)));
+    void* work[2] = {B.get(field), B.get(field)};
+    void* lam[2] = {B.get(lamf), B.get(lamf)};
+    if (!in || !gdev || !part || !work[0] || !work[1] || !lam[0] || !lam[1])
+        return fail(h, KBC_ERR_NOMEM, "adjoint buffers");
+    // checkpoints and segment states in two slabs
+    char* ckslab = nseg ? static_cast<char*>(B.get(field * (size_t)nseg)) : nullptr;
+    char* segslab = seglen > 1 ? static_cast<char*>(B.get(field * (size_t)(seglen - 1))) : nullptr;
+    if ((nseg && !ckslab) || (seglen > 1 && !segslab))
+        return fail(h, KBC_ERR_NOMEM, "adjoint checkpoint storage");
+    cudaError_t e = cudaMemcpyAsync(in, rho0, n * sizeof(double), cudaMemcpyDefault, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(in + n, u0, 2 * n * sizeof(double), cudaMemcpyDefault, h->stream);
+    if (e == cudaSuccess && objective == 1)
+        e = cudaMemcpyAsync(in + 3 * n, u_target, 2 * n * sizeof(double), cudaMemcpyDefault, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(part, 0, (size_t)(2 * nb + 8) * sizeof(double), h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "adjoint inputs");
+    StepArgs a = args_of(h);
+    e = by_codec(h->dtype, [&](auto c) {
+        using C = decltype(c);
+        return launch_init<C>(in, in + n, in + 2 * n, work[0], a, false, h->stream, h->num_sms);
+    });
+    if (e != cudaSuccess) return cuda_fail(h, e, "adjoint init");
+    // forward sweep, keeping g^{sK}
+    int cur = 0;
+    for (int t = 0; t < nsteps; ++t) {
+        if (t % K == 0) {
+            e = cudaMemcpyAsync(ckslab + field * (size_t)(t / K), work[cur], field,
+                                cudaMemcpyDeviceToDevice, h->stream);
+            if (e != cudaSuccess) return cuda_fail(h, e, "checkpoint copy");
+        }
+        rc = step_into(h, work[cur], work[cur ^ 1]);
+        if (rc) return rc;
+        cur ^= 1;
+    }
+    const void* gN = work[cur];
+    // J and lambda^N
+    a = args_of(h);
+    e = by_codec(h->dtype, [&](auto c) {
+        using C = decltype(c);
+        return launch_adj_objective<C>(gN, objective == 1 ? in + 3 * n : nullptr,
+                                       objective == 1 ? in + 4 * n : nullptr, objective, lam[0],
+                                       part, nb, a, h->stream);
+    });
+    if (e != cudaSuccess) return cuda_fail(h, e, "objective");
+    // the handle keeps g^N
+    e = cudaMemcpyAsync(h->buf[h->cur], gN, field, cudaMemcpyDeviceToDevice, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "final state copy");
+    h->initialized = true;
+    // reverse sweep over segments, recomputing each from its checkpoint
+    int lc = 0;
+    for (int sgi = nseg - 1; sgi >= 0; --sgi) {
+        const int n0 = sgi * K;
+        const int n1 = (n0 + K < nsteps) ? n0 + K : nsteps;
+        const int len = n1 - n0;
+        std::vector<const void*> states((size_t)len);
+        states[0] = ckslab + field * (size_t)sgi;
+        for (int j = 1; j < len; ++j) {
+            void* dst = segslab + field * (size_t)(j - 1);
+            rc = step_into(h, states[j - 1], dst);
+            if (rc) return rc;
+            states[j] = dst;
+        }
+        for (int t = n1 - 1; t >= n0; --t) {
+            a = args_of(h);
+            e = by_codec(h->dtype, [&](auto c) {
+                using C = decltype(c);
+                return launch_adj_step<C>(h->variant, states[t - n0], lam[lc], lam[lc ^ 1],
+                                          part + nb, nb, a, h->stream);
+            });
+            if (e != cudaSuccess) return cuda_fail(h, e, "adjoint step");
+            lc ^= 1;
+        }
+    }
+    // dJ/du0 and the two sums
+    e = by_codec(h->dtype, [&](auto c) {
+        using C = decltype(c);
+        return launch_adj_grad_u0<C>(in, in + n, in + 2 * n, lam[lc], gdev, gdev + n, a, h->stream,
+                                     h->num_sms);
+    });
+    if (e != cudaSuccess) return cuda_fail(h, e, "grad u0");
+    double* sums = part + 2 * nb;
+    sum_partials<<<1, 256, 0, h->stream>>>(part, nb, sums);
+    sum_partials<<<1, 256, 0, h->stream>>>(part + nb, nb, sums + 1);
+    e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(grad_u0, gdev, 2 * n * sizeof(double), cudaMemcpyDefault, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->flag_host + 0, h->flag_dev, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    double host_sums[2] = {0.0, 0.0};
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(host_sums, sums, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "adjoint outputs");
+    rc = wait_stream(h, 0);
+    if (rc) return rc;
+    *J = host_sums[0];
+    *grad_beta = host_sums[1];
+    if (*h->flag_host) return fail(h, KBC_ERR_NONFINITE, "non-finite populations in the forward sweep");
+    return KBC_OK;
 }
 
 int kbc_bytes_per_update(kbc_handle h, double* bytes)

@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 
+#include "kbc_adjoint.cuh"
 #include "kbc_kernels.cuh"
 
 namespace kbc {
@@ -139,6 +140,51 @@ cudaError_t launch_diag(const void* src, double* part, int nblocks, double* out,
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- adjoint
+
+inline int adj_blocks(long long total, int num_sms) { return grid_for(total, 256, num_sms, 8); }
+
+template <class C>
+cudaError_t launch_adj_step(int variant, const void* g, const void* lam_in, void* lam_out,
+                            double* part, int nblocks, const StepArgs& a, cudaStream_t s)
+{
+    using S = typename C::S;
+    using T = typename C::T;
+    const S* gp = static_cast<const S*>(g);
+    const T* li = static_cast<const T*>(lam_in);
+    T* lo = static_cast<T*>(lam_out);
+    switch (variant) {
+    case kLBGK: adj_step<kLBGK, C><<<nblocks, 256, 0, s>>>(gp, li, lo, part, a); break;
+    case kA: adj_step<kA, C><<<nblocks, 256, 0, s>>>(gp, li, lo, part, a); break;
+    case kB: adj_step<kB, C><<<nblocks, 256, 0, s>>>(gp, li, lo, part, a); break;
+    case kC: adj_step<kC, C><<<nblocks, 256, 0, s>>>(gp, li, lo, part, a); break;
+    case kD: adj_step<kD, C><<<nblocks, 256, 0, s>>>(gp, li, lo, part, a); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <class C>
+cudaError_t launch_adj_objective(const void* g, const double* tx, const double* ty, int objective,
+                                 void* lam, double* part, int nblocks, const StepArgs& a,
+                                 cudaStream_t s)
+{
+    adj_objective<C><<<nblocks, 256, 0, s>>>(static_cast<const typename C::S*>(g), tx, ty, objective,
+                                             static_cast<typename C::T*>(lam), part, a);
+    return cudaGetLastError();
+}
+
+template <class C>
+cudaError_t launch_adj_grad_u0(const double* rho0, const double* ux0, const double* uy0,
+                               const void* lam, double* gx, double* gy, const StepArgs& a,
+                               cudaStream_t s, int num_sms)
+{
+    const long long total = (long long)a.nx * a.ny;
+    adj_grad_u0<C><<<grid_for(total, 256, num_sms, 16), 256, 0, s>>>(
+        rho0, ux0, uy0, static_cast<const typename C::T*>(lam), gx, gy, a);
+    return cudaGetLastError();
+}
+
 // explicit instantiations live in the per-codec translation units
 #define KBC_DECLARE_CODEC(C)                                                                   \
     extern template cudaError_t launch_step<C>(const Launch&);                                \
@@ -154,7 +200,17 @@ cudaError_t launch_diag(const void* src, double* part, int nblocks, double* out,
     extern template cudaError_t launch_diag<C>(const void*, double*, int, double*, int,       \
                                                const StepArgs&, cudaStream_t);                \
     extern template cudaError_t launch_probe<C>(const void*, const long long*, int, double*,  \
-                                                int*, const StepArgs&, cudaStream_t, int);
+                                                int*, const StepArgs&, cudaStream_t, int);    \
+    extern template cudaError_t launch_adj_step<C>(int, const void*, const void*, void*,      \
+                                                   double*, int, const StepArgs&,             \
+                                                   cudaStream_t);                             \
+    extern template cudaError_t launch_adj_objective<C>(const void*, const double*,           \
+                                                        const double*, int, void*, double*,   \
+                                                        int, const StepArgs&, cudaStream_t);  \
+    extern template cudaError_t launch_adj_grad_u0<C>(const double*, const double*,           \
+                                                      const double*, const void*, double*,    \
+                                                      double*, const StepArgs&, cudaStream_t, \
+                                                      int);
 
 #define KBC_DEFINE_CODEC(C)                                                                    \
     template cudaError_t launch_step<C>(const Launch&);                                       \
@@ -169,7 +225,15 @@ cudaError_t launch_diag(const void* src, double* part, int nblocks, double* out,
     template cudaError_t launch_diag<C>(const void*, double*, int, double*, int,              \
                                         const StepArgs&, cudaStream_t);                       \
     template cudaError_t launch_probe<C>(const void*, const long long*, int, double*, int*,   \
-                                         const StepArgs&, cudaStream_t, int);
+                                         const StepArgs&, cudaStream_t, int);                 \
+    template cudaError_t launch_adj_step<C>(int, const void*, const void*, void*, double*,    \
+                                            int, const StepArgs&, cudaStream_t);              \
+    template cudaError_t launch_adj_objective<C>(const void*, const double*, const double*,   \
+                                                 int, void*, double*, int, const StepArgs&,   \
+                                                 cudaStream_t);                               \
+    template cudaError_t launch_adj_grad_u0<C>(const double*, const double*, const double*,   \
+                                               const void*, double*, double*,                 \
+                                               const StepArgs&, cudaStream_t, int);
 
 #ifndef KBC_CODEC_TU
 KBC_DECLARE_CODEC(CodecF64)

@@ -1,0 +1,126 @@
+"""GPU adjoint: gradients of J(u0, beta) from the hand-written CUDA reverse
+sweep against (1) the oracle's reverse sweep, whose local derivatives are
+complex steps of the oracle's own collision, (2) central finite differences
+of the GPU forward map in FP64, (3) itself under different checkpoint
+intervals, and (4) the FP32 adjoint against the FP64 one."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O  # noqa: E402
+from paper_1507_02509_gb300 import Lattice, capi, flows  # noqa: E402
+from paper_1507_02509_gb300.autograd import kbc_objective  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+OV = {"lbgk": O.LBGK, "A": O.A, "B": O.B, "C": O.C, "D": O.D}
+
+
+def _case(n, seed, k0=2.0, urms=0.05):
+    rho, ux, uy = flows.turbulence(n, k0=k0, urms=urms, seed=seed, kcut=max(2, n // 4))
+    rng = np.random.default_rng(seed + 1)
+    rho = rho + 0.01 * rng.standard_normal(rho.shape)
+    tx = 0.03 * rng.standard_normal((n, n))
+    ty = 0.03 * rng.standard_normal((n, n))
+    return rho, ux, uy, tx, ty
+
+
+def _gpu_adjoint(variant, dtype, beta, rho, ux, uy, steps, K, objective, tx=None, ty=None):
+    ny, nx = rho.shape
+    lat = Lattice(nx, ny, variant=variant, beta=beta, dtype=dtype)
+    u = np.ascontiguousarray(np.stack((ux, uy)))
+    tgt = np.ascontiguousarray(np.stack((tx, ty))) if objective == 1 else None
+    g = np.empty((2, ny, nx))
+    J, gb = capi.kbc_adjoint(lat.h, np.ascontiguousarray(rho), u, steps, K, objective, tgt, g)
+    lat.close()
+    return J, g, gb
+
+
+@pytest.mark.parametrize("objective", [0, 1])
+@pytest.mark.parametrize("variant", ["lbgk", "A", "B", "C", "D"])
+def test_adjoint_matches_oracle_adjoint(variant, objective):
+    """16x16, 12 steps, FP64: J to 1e-13 and gradients to 1e-9 (relative, in
+    the max norm) against the oracle's complex-step reverse sweep."""
+    n, steps, beta = 16, 12, 0.95
+    rho, ux, uy, tx, ty = _case(n, 5)
+    J, g, gb = _gpu_adjoint(variant, "f64", beta, rho, ux, uy, steps, 5, objective, tx, ty)
+    Jo, gxo, gyo, gbo = O.adjoint(OV[variant], beta, rho, ux, uy, steps, objective, tx, ty)
+    assert J == pytest.approx(Jo, rel=1e-13)
+    go = np.stack((gxo, gyo))
+    assert np.max(np.abs(g - go)) <= 1e-9 * np.max(np.abs(go))
+    assert gb == pytest.approx(gbo, rel=1e-9)
+
+
+@pytest.mark.parametrize("variant", ["B", "C"])
+def test_adjoint_matches_finite_differences(variant):
+    """64x64 (vector-row kernel), 40 steps, FP64: dJ/du0 at three nodes and
+    dJ/dbeta against central differences of the GPU forward map (h = 1e-6
+    relative agreement 1e-6)."""
+    n, steps, beta = 64, 40, 0.97
+    rho, ux, uy, tx, ty = _case(n, 8, k0=3.0, urms=0.04)
+    J, g, gb = _gpu_adjoint(variant, "f64", beta, rho, ux, uy, steps, 10, 1, tx, ty)
+
+    def J_of(ux_, uy_, b):
+        lat = Lattice(n, n, variant=variant, beta=b, dtype="f64")
+        lat.init(rho, ux_, uy_).step(steps)
+        _, vx, vy = (t.cpu().numpy() for t in lat.moments())
+        lat.close()
+        return 0.5 * np.sum((vx - tx) ** 2 + (vy - ty) ** 2)
+
+    assert J == pytest.approx(J_of(ux, uy, beta), rel=1e-12)
+    h = 1e-6
+    for (yy, xx) in ((3, 5), (40, 17), (63, 63)):
+        for comp in (0, 1):
+            up, um = (ux.copy(), uy.copy()), (ux.copy(), uy.copy())
+            up[comp][yy, xx] += h
+            um[comp][yy, xx] -= h
+            fd = (J_of(*up, beta) - J_of(*um, beta)) / (2 * h)
+            assert g[comp, yy, xx] == pytest.approx(fd, rel=1e-6, abs=1e-9 * abs(J)), (yy, xx, comp)
+    fd = (J_of(ux, uy, beta + h) - J_of(ux, uy, beta - h)) / (2 * h)
+    assert gb == pytest.approx(fd, rel=1e-6)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_checkpoint_interval_does_not_change_gradients(dtype):
+    """Recomputed segments are bit-identical to the forward sweep, so the
+    gradients do not depend on the checkpoint interval."""
+    n, steps = 128, 30
+    rho, ux, uy, tx, ty = _case(n, 3, k0=4.0)
+    out = [_gpu_adjoint("B", dtype, 0.98, rho, ux, uy, steps, K, 0) for K in (1, 7, 30, 100)]
+    for J, g, gb in out[1:]:
+        assert J == out[0][0] and gb == out[0][2]
+        assert np.array_equal(g, out[0][1])
+
+
+def test_autograd_function_returns_adjoint_gradients():
+    n, steps = 64, 20
+    rho, ux, uy, tx, ty = _case(n, 4, k0=3.0)
+    u0 = torch.tensor(np.stack((ux, uy)), device="cuda", requires_grad=True)
+    beta = torch.tensor(0.96, dtype=torch.float64, requires_grad=True)
+    tgt = torch.tensor(np.stack((tx, ty)), device="cuda")
+    J = kbc_objective(u0, beta, rho0=torch.tensor(rho, device="cuda"), variant="B",
+                      dtype="f64", steps=steps, ckpt_every=8, objective="misfit", u_target=tgt)
+    (3.0 * J).backward()
+    Jd, g, gb = _gpu_adjoint("B", "f64", 0.96, rho, ux, uy, steps, 8, 1, tx, ty)
+    assert float(J) == Jd
+    assert np.array_equal(u0.grad.cpu().numpy(), 3.0 * g)
+    assert float(beta.grad) == pytest.approx(3.0 * gb, rel=1e-15)
+
+
+def test_fp32_adjoint_tracks_fp64_on_512():
+    """Adjoint configuration: 512^2 periodic, seeded random velocity (k0 = 8),
+    KBC B, checkpoints every 100 steps; gradient of the final kinetic energy.
+    FP32 storage/arithmetic against the FP64 adjoint (stated, bounded)."""
+    n, steps, K = 512, 400, 100
+    rho, ux, uy = flows.turbulence(n, k0=8, urms=0.03, seed=11)
+    nu = n * 0.03 / 5000.0
+    beta = 1.0 / (6 * nu + 1)
+    J64, g64, gb64 = _gpu_adjoint("B", "f64", beta, rho, ux, uy, steps, K, 0)
+    J32, g32, gb32 = _gpu_adjoint("B", "f32", beta, rho, ux, uy, steps, K, 0)
+    rel_g = np.max(np.abs(g32 - g64)) / np.max(np.abs(g64))
+    print(f"512^2 {steps} steps: J rel {abs(J32 - J64) / J64:.2e}, grad_u0 rel {rel_g:.2e}, "
+          f"grad_beta rel {abs(gb32 - gb64) / abs(gb64):.2e}")
+    assert abs(J32 - J64) <= 1e-5 * J64
+    assert rel_g < 1e-2
+    assert abs(gb32 - gb64) <= 1e-2 * abs(gb64)
