@@ -95,8 +95,8 @@ int kbc_set_allocator(kbc_alloc_fn alloc, kbc_free_fn release, void* user);
  * kinematic viscosity by nu = cs^2 (1/(2 beta) - 1/2), cs^2 = 1/3
  * (Eq. viscosity).  Requirements: nx, ny >= 1, nx * ny <= 2^31 - 1,
  * 0 < beta <= 1, variant and dtype from their enums; else KBC_ERR_ARG.
- * Grids with nx a multiple of the vector row width (128 for F32, 64 for F64,
- * 256 for F16) take the vectorised row kernel, all others a per-node kernel
+ * Grids with nx a multiple of the vector row width (128 for F32 and F16, 64
+ * for F64) take the vectorised row kernel, all others a per-node kernel
  * with the same arithmetic.  *out is NULL on failure. */
 int kbc_create(int nx, int ny, int variant, double beta, int dtype, kbc_handle* out);
 

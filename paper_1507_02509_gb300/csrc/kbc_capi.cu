@@ -157,7 +157,10 @@ bool is_device_ptr(const void* p)
 }
 
 size_t elem_size(int dtype) { return dtype == KBC_F64 ? 8 : dtype == KBC_F32_DEV ? 4 : 2; }
-int vec_width(int dtype) { return dtype == KBC_F64 ? 2 : dtype == KBC_F32_DEV ? 4 : 8; }
+int vec_width(int dtype)
+{
+    return dtype == KBC_F64 ? CodecF64::kVec : dtype == KBC_F32_DEV ? CodecF32::kVec : CodecF16::kVec;
+}
 
 StepArgs args_of(const kbc_ctx* h)
 {

@@ -213,14 +213,14 @@ __device__ __forceinline__ T collide(T (&d)[9], const CollideParams<T>& p, T& rh
         P[7] = eq_poly<7>(ux, uy, usq15);
         T x[9], w[9];
 #pragma unroll
-        for (int i = 0; i < 9; ++i) x[i] = T(1) + P[i];
-        inv9(x, w);  // rho / f^eq_i = (1 / W_i) w_i
+        for (int i = 0; i < 9; ++i) x[i] = fmaT(T(wgt(i)), P[i], T(wgt(i)));  // f^eq_i / rho
+        inv9(x, w);  // w_i = rho / f^eq_i
         T dh[9];
         T sh = T(0), hh = T(0);
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             dh[i] = df[i] - ds[i];
-            const T t = dh[i] * (T(inv_wgt(i)) * w[i]);
+            const T t = dh[i] * w[i];
             sh = fmaT(ds[i], t, sh);
             hh = fmaT(dh[i], t, hh);
         }

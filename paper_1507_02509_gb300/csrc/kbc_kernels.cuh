@@ -197,10 +197,17 @@ step_rows(const typename C::S* __restrict__ src, typename C::S* __restrict__ dst
     const long long o = (long long)y * a.nx + x0;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-        S out[NV];
+        if constexpr (std::is_same<C, CodecF16>::value && NV % 2 == 0) {
+            unsigned pk[NV / 2];
 #pragma unroll
-        for (int k = 0; k < NV; ++k) out[k] = C::encode(f[k][i], i, a.cs);
-        Vec<S, NV>::store(dst + (long long)i * a.plane + o, out);
+            for (int k = 0; k < NV; k += 2) pk[k / 2] = C::encode2(f[k][i], f[k + 1][i], i, a.cs);
+            Vec<unsigned, NV / 2>::store(reinterpret_cast<unsigned*>(dst + (long long)i * a.plane + o), pk);
+        } else {
+            S out[NV];
+#pragma unroll
+            for (int k = 0; k < NV; ++k) out[k] = C::encode(f[k][i], i, a.cs);
+            Vec<S, NV>::store(dst + (long long)i * a.plane + o, out);
+        }
     }
 }
 

@@ -39,10 +39,12 @@ struct CodecScale {
 //   encode(d, i, c)     -> stored element
 //   to_f64(s, i, c)     -> d_i in double (exact for F64/F32 storage)
 //   from_f64(d, i, c)   -> stored element from a double deviation
+// kVec: nodes per thread of the vector-row kernel (kVec * sizeof(S) bytes
+// per load/store; 16 for F64/F32, 8 for F16, which keeps F16 registers low).
 struct CodecF64 {
     using S = double;
     using T = double;
-    static constexpr int kVec = 2;  // elements per 16-byte vector
+    static constexpr int kVec = 2;
     __device__ __forceinline__ static T decode(S s, int, const CodecScale&) { return s; }
     __device__ __forceinline__ static S encode(T d, int, const CodecScale&) { return d; }
     __device__ __forceinline__ static double to_f64(S s, int, const CodecScale&) { return s; }
@@ -64,7 +66,7 @@ struct CodecF32 {
 struct CodecF16 {
     using S = unsigned short;
     using T = float;
-    static constexpr int kVec = 8;
+    static constexpr int kVec = 4;
     __device__ __forceinline__ static T decode(S s, int i, const CodecScale& c)
     {
         return __half2float(__ushort_as_half(s)) * ((float)wgt(i) * c.inv_scale);
@@ -72,6 +74,13 @@ struct CodecF16 {
     __device__ __forceinline__ static S encode(T d, int i, const CodecScale& c)
     {
         return __half_as_ushort(__float2half_rn(d * ((float)inv_wgt(i) * c.scale)));
+    }
+    // two populations of the same plane in one packed conversion
+    __device__ __forceinline__ static unsigned encode2(T d0, T d1, int i, const CodecScale& c)
+    {
+        const float k = (float)inv_wgt(i) * c.scale;
+        const __half2 h = __floats2half2_rn(d0 * k, d1 * k);
+        return *reinterpret_cast<const unsigned*>(&h);
     }
     __device__ __forceinline__ static double to_f64(S s, int i, const CodecScale& c)
     {
