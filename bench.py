@@ -153,6 +153,48 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+class Ranks:
+    """Replica bookkeeping for torchrun launches: one rank per GPU, each rank
+    advancing its own grid; timing is the maximum over ranks after a
+    barrier, and the job's value is the units of all ranks over that time."""
+
+    def __init__(self):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.dist = None
+
+    def init(self, backend: str):
+        if self.world > 1:
+            import torch.distributed as dist
+
+            dist.init_process_group(backend)
+            self.dist = dist
+
+    def barrier(self):
+        if self.dist is not None:
+            self.dist.barrier()
+
+    def max(self, x: float, device) -> float:
+        if self.dist is None:
+            return x
+        import torch
+
+        t = torch.tensor([x], dtype=torch.float64, device=device)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.dist is not None:
+            self.dist.destroy_process_group()
+            self.dist = None
+
+
+def job_mlups(world: int, nodes: int, steps: int, seconds: float) -> float:
+    """Whole-job throughput: all ranks' node updates over the slowest rank's time."""
+    return world * nodes * steps / seconds / 1e6
+
+
 def reynolds_viscosity(n: int, urms: float = 0.03, re: float = 1e5):
     from paper_1507_02509_gb300 import viscosity_for_reynolds
 
@@ -199,18 +241,14 @@ def time_steps(lat, steps, stream):
 
 
 def run_ours(args):
-    import numpy as np
     import torch
-    import torch.distributed as dist
 
     from paper_1507_02509_gb300 import Lattice, beta_from_viscosity, capi, flows
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        dist.init_process_group("nccl")
+    ranks = Ranks()
+    world, rank, local = ranks.world, ranks.rank, ranks.local
     torch.cuda.set_device(local)
+    ranks.init("nccl")
     stream = torch.cuda.current_stream()
     capi.load()
 
@@ -220,16 +258,10 @@ def run_ours(args):
     rho, ux, uy = flows.turbulence(n, k0=16, urms=0.03, seed=args.seed + rank,
                                    backend="torch", device=f"cuda:{local}")
 
-    def barrier():
-        if world > 1:
-            dist.barrier()
+    barrier = ranks.barrier
 
     def max_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        t = torch.tensor([x], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return ranks.max(x, "cuda")
 
     # ---- headline: default workload
     lat = Lattice(n, n, variant=args.variant, beta=beta, dtype=args.dtype)
@@ -246,7 +278,7 @@ def run_ours(args):
     t = max_over_ranks(t)
     guard_on = args.dtype != "f64" and args.variant != "lbgk"
     launches_per_step = 2 if guard_on else 1
-    value = world * n * n * args.steps / t / 1e6
+    value = job_mlups(world, n * n, args.steps, t)
 
     # ---- roofline: the step kernel alone (guard pass off), same launch shape
     bpu = DTYPE_BYTES[args.dtype] * 18
@@ -287,7 +319,7 @@ def run_ours(args):
         barrier()
         hb = h_rho.numel() * 8 + h_u.numel() * 8
         db = o_rho.numel() * 8 + o_u.numel() * 8
-        e2e = {"value": round(world * n * n * args.steps / te / 1e6, 1), "unit": UNIT,
+        e2e = {"value": round(job_mlups(world, n * n, args.steps, te), 1), "unit": UNIT,
                "h2d_bytes_per_step": hb // args.steps, "d2h_bytes_per_step": db // args.steps,
                "what": ("kbc_init from pinned host rho,u + kbc_step(K) + kbc_moments to pinned "
                         "host; copies amortised over the K steps")}
@@ -347,15 +379,14 @@ def run_ours(args):
             "clocks": clk.summary(), "extras": extras,
         }
         print(json.dumps(line), flush=True)
-    if world > 1:
-        dist.destroy_process_group()
+    ranks.close()
 
 
 def run_reference(args):
     """The oracle on the host cores: each step is one oracle step of a
     1024^2 periodic field of the same workload family."""
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
+    ranks = Ranks()
+    world, rank = ranks.world, ranks.rank
     if rank != 0:
         return
     import oracle
