@@ -110,6 +110,16 @@ int kbc_set_stream(kbc_handle h, void* cuda_stream);
  * KBC_LBGK, whose mirror state has no gamma. */
 int kbc_set_gamma_mode(kbc_handle h, int mode, double gamma_fixed);
 
+/* Kernel used by kbc_step (all three share the collision arithmetic, so they
+ * give identical bits):
+ *   KBC_KERNEL_AUTO  (default) the persistent bulk-copy kernel (F32/F16 with
+ *                    nx a multiple of 1024), else the vector-row kernel
+ *                    (nx a multiple of its row width), else the per-node one;
+ *   KBC_KERNEL_ROWS  the vector-row kernel where nx allows, else per-node;
+ *   KBC_KERNEL_NODES the per-node kernel. */
+enum kbc_kernel { KBC_KERNEL_AUTO = 0, KBC_KERNEL_ROWS = 1, KBC_KERNEL_NODES = 2 };
+int kbc_set_kernel(kbc_handle h, int kernel);
+
 /* Threshold on <dh|dh> (entropic scalar product of Sec. 4, computed with the
  * weights rho/f^eq_i) below which an F32/F16 node is recomputed entirely in
  * FP64 from its stored populations by a second pass.  0 disables the pass.

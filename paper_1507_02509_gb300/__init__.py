@@ -122,6 +122,12 @@ class Lattice:
         else:
             capi.kbc_set_gamma_mode(self.h, KBC_GAMMA_FIXED, float(gamma_fixed))
 
+    def set_kernel(self, kernel: str):
+        """"auto" (bulk-copy kernel where possible), "rows" or "nodes"."""
+        k = {"auto": capi.KBC_KERNEL_AUTO, "rows": capi.KBC_KERNEL_ROWS,
+             "nodes": capi.KBC_KERNEL_NODES}[kernel]
+        capi.kbc_set_kernel(self.h, k)
+
     def set_guard(self, threshold: float):
         capi.kbc_set_guard(self.h, threshold)
 

@@ -21,6 +21,7 @@ KBC_GAMMA_ENTROPIC, KBC_GAMMA_FIXED = 0, 1
 KBC_OK, KBC_ERR_ARG, KBC_ERR_CUDA, KBC_ERR_NOMEM = 0, -1, -2, -3
 KBC_ERR_NONFINITE, KBC_ERR_TIMEOUT, KBC_ERR_STATE = -4, -5, -6
 KBC_DIAG_N = 10
+KBC_KERNEL_AUTO, KBC_KERNEL_ROWS, KBC_KERNEL_NODES = 0, 1, 2
 
 STATUS_NAMES = {
     0: "KBC_OK", -1: "KBC_ERR_ARG", -2: "KBC_ERR_CUDA", -3: "KBC_ERR_NOMEM",
@@ -39,6 +40,7 @@ SIGNATURES = {
     "kbc_destroy": (_i, [_vp]),
     "kbc_set_stream": (_i, [_vp, _vp]),
     "kbc_set_gamma_mode": (_i, [_vp, _i, _d]),
+    "kbc_set_kernel": (_i, [_vp, _i]),
     "kbc_set_guard": (_i, [_vp, _d]),
     "kbc_guard_count": (_i, [_vp, ctypes.POINTER(ctypes.c_longlong)]),
     "kbc_set_f16_scale": (_i, [_vp, _d]),
@@ -134,6 +136,10 @@ def kbc_set_stream(h, stream):
 
 def kbc_set_gamma_mode(h, mode: int, gamma_fixed: float = 2.0):
     return check(h, load().kbc_set_gamma_mode(h, int(mode), float(gamma_fixed)))
+
+
+def kbc_set_kernel(h, kernel: int):
+    return check(h, load().kbc_set_kernel(h, int(kernel)))
 
 
 def kbc_set_guard(h, threshold: float):

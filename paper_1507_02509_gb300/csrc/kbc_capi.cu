@@ -108,6 +108,7 @@ struct kbc_ctx {
     void* stage = nullptr;       // device staging for host pointers
     size_t stage_bytes = 0;
     bool initialized = false;
+    int kernel = KBC_KERNEL_AUTO;
     cudaStream_t stream = nullptr;
     Allocator al;
     std::string err;
@@ -243,7 +244,8 @@ static int step_into(kbc_handle h, const void* src, void* dst)
 {
     Launch L;
     L.variant = h->variant;
-    L.rows = (h->nx % (32 * vec_width(h->dtype))) == 0;
+    L.rows = h->kernel != KBC_KERNEL_NODES && (h->nx % (32 * vec_width(h->dtype))) == 0;
+    L.tma = h->kernel == KBC_KERNEL_AUTO && h->dtype != KBC_F64 && (h->nx % kTmaTile) == 0;
     L.stream = h->stream;
     L.num_sms = h->num_sms;
     const bool guard_on = h->dtype != KBC_F64 && h->variant != KBC_LBGK &&
@@ -463,6 +465,14 @@ int kbc_set_gamma_mode(kbc_handle h, int mode, double gamma_fixed)
     return KBC_OK;
 }
 
+int kbc_set_kernel(kbc_handle h, int kernel)
+{
+    if (!h) return KBC_ERR_ARG;
+    if (kernel < KBC_KERNEL_AUTO || kernel > KBC_KERNEL_NODES) return fail(h, KBC_ERR_ARG, "bad kernel");
+    h->kernel = kernel;
+    return KBC_OK;
+}
+
 int kbc_set_guard(kbc_handle h, double threshold)
 {
     if (!h) return KBC_ERR_ARG;
@@ -553,7 +563,8 @@ int kbc_step(kbc_handle h, int nsteps)
     if (rc) return rc;
     if (nsteps < 0) return fail(h, KBC_ERR_ARG, "nsteps must be >= 0");
     if (!h->initialized) return fail(h, KBC_ERR_STATE, "field not initialised");
-    if (*h->flag_host) return fail(h, KBC_ERR_NONFINITE, "non-finite populations detected");
+    if (h->flag_host[0] & 2) return fail(h, KBC_ERR_TIMEOUT, "a device-side wait ran out");
+    if (h->flag_host[0]) return fail(h, KBC_ERR_NONFINITE, "non-finite populations detected");
     if (nsteps == 0) return KBC_OK;
     for (int s = 0; s < nsteps; ++s) {
         rc = step_into(h, h->buf[h->cur], h->buf[h->cur ^ 1]);
@@ -572,7 +583,8 @@ int kbc_sync(kbc_handle h, double timeout_s)
     if (rc) return rc;
     rc = wait_stream(h, timeout_s);
     if (rc) return rc;
-    if (*h->flag_host) return fail(h, KBC_ERR_NONFINITE, "non-finite populations detected");
+    if (h->flag_host[0] & 2) return fail(h, KBC_ERR_TIMEOUT, "a device-side wait ran out");
+    if (h->flag_host[0]) return fail(h, KBC_ERR_NONFINITE, "non-finite populations detected");
     return KBC_OK;
 }
 
@@ -800,7 +812,8 @@ int kbc_adjoint(kbc_handle h, const double* rho0, const double* u0, int nsteps, 
     if (rc) return rc;
     *J = host_sums[0];
     *grad_beta = host_sums[1];
-    if (*h->flag_host) return fail(h, KBC_ERR_NONFINITE, "non-finite populations in the forward sweep");
+    if (h->flag_host[0] & 2) return fail(h, KBC_ERR_TIMEOUT, "a device-side wait ran out");
+    if (h->flag_host[0]) return fail(h, KBC_ERR_NONFINITE, "non-finite populations in the forward sweep");
     return KBC_OK;
 }
 

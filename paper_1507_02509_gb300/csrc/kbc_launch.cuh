@@ -6,6 +6,7 @@
 
 #include "kbc_adjoint.cuh"
 #include "kbc_kernels.cuh"
+#include "kbc_tma.cuh"
 
 namespace kbc {
 
@@ -15,6 +16,7 @@ struct Launch {
     StepArgs a;
     int variant;
     bool rows;      // vectorised row kernel (nx % (32 * kVec) == 0)
+    bool tma;       // persistent bulk-copy kernel (nx % kTmaTile == 0, F32/F16)
     bool fixup;     // FP64 re-evaluation pass after the step
     cudaStream_t stream;
     int num_sms;
@@ -37,6 +39,33 @@ cudaError_t launch_step_v(const Launch& L)
     using S = typename C::S;
     const S* src = static_cast<const S*>(L.src);
     S* dst = static_cast<S*>(L.dst);
+    if constexpr (!std::is_same<C, CodecF64>::value) {
+        if (L.tma) {
+            constexpr size_t smem = tma_smem_bytes<S, kTmaTile>();
+            constexpr int threads = kTmaTile / C::kVec;
+            static int per_sm = 0;  // resident CTAs per SM, from the occupancy calculator
+            if (per_sm == 0) {
+                cudaError_t e = cudaFuncSetAttribute(step_tma<VAR, C, kTmaTile>,
+                                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                     (int)smem);
+                if (e != cudaSuccess) return e;
+                int n = 0;
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_tma<VAR, C, kTmaTile>,
+                                                                  threads, smem);
+                if (e != cudaSuccess) return e;
+                per_sm = n > 0 ? n : 1;
+            }
+            const long long tiles = (long long)(L.a.nx / kTmaTile) * L.a.ny;
+            long long grid = (long long)L.num_sms * per_sm;
+            if (grid > tiles) grid = tiles;
+            step_tma<VAR, C, kTmaTile><<<(unsigned)grid, threads, smem, L.stream>>>(src, dst, L.a);
+            if constexpr (VAR != kLBGK) {
+                if (L.fixup)
+                    step_fixup<VAR, C><<<L.num_sms * 2, kNodeBlock, 0, L.stream>>>(src, dst, L.a);
+            }
+            return cudaGetLastError();
+        }
+    }
     if (L.rows) {
         constexpr int NV = C::kVec;
         const int nbx = (L.a.nx + kRowBlock * NV - 1) / (kRowBlock * NV);

@@ -53,7 +53,8 @@ def _one_step(nx, ny, variant, dtype, seed, beta=0.97, steps=1):
 # shapes: vector-row kernel over several warps and blocks with a partial last
 # block (640 = 5 x 128 for f32, 10 x 64 for f64), odd row counts, and the
 # per-node kernel for ragged widths; 1 x 1 wraps every population onto itself
-SHAPES = [(640, 37), (768, 6), (37, 23), (130, 5), (3, 3), (1, 1), (2, 7)]
+SHAPES = [(640, 37), (768, 6), (37, 23), (130, 5), (3, 3), (1, 1), (2, 7), (1024, 5), (2048, 3),
+          (1024, 1)]
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
@@ -67,7 +68,7 @@ def test_one_step_matches_oracle(shape, variant, dtype):
 
 
 @pytest.mark.parametrize("variant", VARIANTS)
-@pytest.mark.parametrize("shape", [(768, 9), (256, 4), (37, 11)])
+@pytest.mark.parametrize("shape", [(768, 9), (256, 4), (37, 11), (1024, 3), (2048, 2)])
 def test_one_step_f16(shape, variant):
     """f16 storage: the GPU result, re-rounded to half, against the oracle
     result of the same stored input (tolerance: a few half ulps of (f-W)/W)."""
@@ -95,6 +96,26 @@ def test_kbc_gamma_two_is_lbgk_bit_for_bit(dtype, shape):
         lat.close()
     for v in "ABCD":
         assert np.array_equal(outs[v], outs["lbgk"]), v
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "f16"])
+@pytest.mark.parametrize("variant", ["lbgk", "B", "C"])
+@pytest.mark.parametrize("shape", [(2048, 6), (1024, 9), (256, 7)])
+def test_kernels_give_identical_bits(shape, variant, dtype):
+    """The bulk-copy, vector-row and per-node kernels share the collision
+    arithmetic: five steps from the same field agree bit for bit."""
+    nx, ny = shape
+    g = representable(random_field(nx, ny, 21), dtype)
+    outs = []
+    for kernel in ("auto", "rows", "nodes"):
+        lat = Lattice(nx, ny, variant=variant, beta=0.97, dtype=dtype)
+        lat.set_kernel(kernel)
+        lat.set_guard(0.0)
+        lat.set_populations(g)
+        lat.step(5)
+        outs.append(lat.populations().cpu().numpy())
+        lat.close()
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
