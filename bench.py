@@ -356,6 +356,47 @@ def run_ours(args):
             del lx
             torch.cuda.empty_cache()
 
+    # ---- the other rows of the path: diagnostics reduction and the adjoint
+    if args.extras:
+        import numpy as np
+
+        lx = Lattice(n, n, variant=args.variant, beta=beta, dtype=args.dtype)
+        lx.init(rho, ux, uy)
+        lx.sync()
+        out = np.zeros(capi.KBC_DIAG_N)
+        t0 = time.perf_counter()
+        for _ in range(3):
+            capi.kbc_diagnostics(lx.h, out)
+        td = (time.perf_counter() - t0) / 3
+        extras["diagnostics"] = {"ms": round(td * 1e3, 3),
+                                 "mlups": round(n * n / td / 1e6, 1),
+                                 "what": "kbc_diagnostics (FP64 reductions incl. gamma) + host read"}
+        lx.close()
+        del lx
+        torch.cuda.empty_cache()
+        # adjoint configuration: 512^2, k0 = 8, KBC B, 2000 steps, checkpoints every 100
+        na, steps_a, ka = 512, 2000, 100
+        ra, xa, ya = flows.turbulence(na, k0=8, urms=0.03, seed=args.seed, backend="torch",
+                                      device=f"cuda:{local}")
+        beta_a = beta_from_viscosity(na * 0.03 / 5000.0)
+        ua = torch.stack((xa, ya)).contiguous()
+        for dt in ("f32", "f64"):
+            la = Lattice(na, na, variant="B", beta=beta_a, dtype=dt)
+            g = torch.empty_like(ua)
+            capi.kbc_adjoint(la.h, ra, ua, 20, 10, 0, None, g)  # warm-up
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            capi.kbc_adjoint(la.h, ra, ua, steps_a, ka, 0, None, g)
+            ta = time.perf_counter() - t0
+            extras[f"adjoint_{dt}"] = {
+                "seconds": round(ta, 3), "steps": steps_a, "ckpt_every": ka, "n": na,
+                "mlups_forward_equiv": round(na * na * steps_a / ta / 1e6, 1),
+                "what": "kbc_adjoint: forward with checkpoints + reverse sweep with segment "
+                        "recompute (3 stream-collide passes per step in all)"}
+            la.close()
+        del ra, xa, ya, ua
+        torch.cuda.empty_cache()
+
     cpu = None
     if args.cpu_baseline and rank == 0:
         rate, cores, k, nc = cpu_oracle_rate(args.steps)

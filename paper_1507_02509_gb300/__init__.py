@@ -123,9 +123,9 @@ class Lattice:
             capi.kbc_set_gamma_mode(self.h, KBC_GAMMA_FIXED, float(gamma_fixed))
 
     def set_kernel(self, kernel: str):
-        """"auto" (bulk-copy kernel where possible), "rows" or "nodes"."""
+        """"auto", "rows", "nodes" or "bulk" (see kbc_set_kernel)."""
         k = {"auto": capi.KBC_KERNEL_AUTO, "rows": capi.KBC_KERNEL_ROWS,
-             "nodes": capi.KBC_KERNEL_NODES}[kernel]
+             "nodes": capi.KBC_KERNEL_NODES, "bulk": capi.KBC_KERNEL_BULK}[kernel]
         capi.kbc_set_kernel(self.h, k)
 
     def set_guard(self, threshold: float):

@@ -21,7 +21,7 @@ KBC_GAMMA_ENTROPIC, KBC_GAMMA_FIXED = 0, 1
 KBC_OK, KBC_ERR_ARG, KBC_ERR_CUDA, KBC_ERR_NOMEM = 0, -1, -2, -3
 KBC_ERR_NONFINITE, KBC_ERR_TIMEOUT, KBC_ERR_STATE = -4, -5, -6
 KBC_DIAG_N = 10
-KBC_KERNEL_AUTO, KBC_KERNEL_ROWS, KBC_KERNEL_NODES = 0, 1, 2
+KBC_KERNEL_AUTO, KBC_KERNEL_ROWS, KBC_KERNEL_NODES, KBC_KERNEL_BULK = 0, 1, 2, 3
 
 STATUS_NAMES = {
     0: "KBC_OK", -1: "KBC_ERR_ARG", -2: "KBC_ERR_CUDA", -3: "KBC_ERR_NOMEM",

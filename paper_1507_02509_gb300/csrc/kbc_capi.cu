@@ -245,7 +245,7 @@ static int step_into(kbc_handle h, const void* src, void* dst)
     Launch L;
     L.variant = h->variant;
     L.rows = h->kernel != KBC_KERNEL_NODES && (h->nx % (32 * vec_width(h->dtype))) == 0;
-    L.tma = h->kernel == KBC_KERNEL_AUTO && h->dtype != KBC_F64 && (h->nx % kTmaTile) == 0;
+    L.tma = h->kernel == KBC_KERNEL_BULK && h->dtype != KBC_F64 && (h->nx % kTmaTile) == 0;
     L.stream = h->stream;
     L.num_sms = h->num_sms;
     const bool guard_on = h->dtype != KBC_F64 && h->variant != KBC_LBGK &&
@@ -468,7 +468,7 @@ int kbc_set_gamma_mode(kbc_handle h, int mode, double gamma_fixed)
 int kbc_set_kernel(kbc_handle h, int kernel)
 {
     if (!h) return KBC_ERR_ARG;
-    if (kernel < KBC_KERNEL_AUTO || kernel > KBC_KERNEL_NODES) return fail(h, KBC_ERR_ARG, "bad kernel");
+    if (kernel < KBC_KERNEL_AUTO || kernel > KBC_KERNEL_BULK) return fail(h, KBC_ERR_ARG, "bad kernel");
     h->kernel = kernel;
     return KBC_OK;
 }
