@@ -63,9 +63,13 @@ enum kbc_variant { KBC_LBGK = 0, KBC_A = 1, KBC_B = 2, KBC_C = 3, KBC_D = 4 };
  *              (kbc_set_f16_scale), arithmetic in float. */
 enum kbc_dtype { KBC_F64 = 0, KBC_F32_DEV = 1, KBC_F16_DEV = 2 };
 
-/* gamma of Eq. result21 (entropic), or a fixed value (2 reproduces LBGK,
- * 1/beta the regularised limit discussed after Eq. dsdh1B). */
-enum kbc_gamma_mode { KBC_GAMMA_ENTROPIC = 0, KBC_GAMMA_FIXED = 1 };
+/* gamma of Eq. result21 (entropic, the paper's choice), a fixed value (2
+ * reproduces LBGK, 1/beta the regularised limit discussed after
+ * Eq. dsdh1B), or the root of the exact entropic condition Eq. result1
+ * (Newton from gamma*, in double precision whatever the storage, by a
+ * per-node kernel; gamma* is kept where an iterate leaves the domain of
+ * positive post-collision populations or 30 iterations pass). */
+enum kbc_gamma_mode { KBC_GAMMA_ENTROPIC = 0, KBC_GAMMA_FIXED = 1, KBC_GAMMA_EXACT = 2 };
 
 enum kbc_status {
     KBC_OK = 0,
@@ -106,8 +110,8 @@ int kbc_destroy(kbc_handle h);
 /* Bind a cudaStream_t (passed as void*); NULL = legacy default stream. */
 int kbc_set_stream(kbc_handle h, void* cuda_stream);
 
-/* gamma mode (enum kbc_gamma_mode) and the fixed gamma it uses.  Ignored by
- * KBC_LBGK, whose mirror state has no gamma. */
+/* gamma mode (enum kbc_gamma_mode) and the fixed gamma it uses (ignored by
+ * the other modes).  Ignored by KBC_LBGK, whose mirror state has no gamma. */
 int kbc_set_gamma_mode(kbc_handle h, int mode, double gamma_fixed);
 
 /* Kernel used by kbc_step (all of them share the collision arithmetic, so
@@ -224,7 +228,8 @@ int kbc_diagnostics_noalloc(int nx, int ny, int variant, double beta, const doub
  * Device memory for the call, from the handle's allocator and released
  * before returning: ceil(nsteps/ckpt_every) + ckpt_every + 1 population
  * fields, two adjoint fields and O(nx ny) doubles.  Synchronises the
- * stream.  Afterwards the handle holds g^nsteps.  Errors: KBC_ERR_ARG,
+ * stream.  Afterwards the handle holds g^nsteps.  The exact-gamma mode is
+ * not differentiated (KBC_ERR_ARG).  Errors: KBC_ERR_ARG,
  * KBC_ERR_NOMEM, KBC_ERR_NONFINITE (the forward sweep blew up). */
 int kbc_adjoint(kbc_handle h, const double* rho0, const double* u0, int nsteps, int ckpt_every,
                 int objective, const double* u_target, double* J, double* grad_u0,

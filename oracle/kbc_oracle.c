@@ -64,19 +64,23 @@ static int kbco_in_s(int variant, int j)
 #define R double
 #define FN(x) x##_r
 #define RE(x) (x)
+#define LOG1P(x) log1p(x)
 #include "kbc_oracle_core.inc"
 #undef R
 #undef FN
 #undef RE
+#undef LOG1P
 
 /* ---- complex instance (complex-step derivatives) ------------------------ */
 #define R double complex
 #define FN(x) x##_c
 #define RE(x) creal(x)
+#define LOG1P(x) clog(1.0 + (x))
 #include "kbc_oracle_core.inc"
 #undef R
 #undef FN
 #undef RE
+#undef LOG1P
 
 static int valid_variant(int v) { return v >= KBCO_LBGK && v <= KBCO_D; }
 
@@ -157,7 +161,7 @@ int kbco_collide_jacobian_batch(int n, int variant, double beta, int gmode,
                                 double gfix, const double* f, double* J,
                                 double* dbeta)
 {
-    if (!valid_variant(variant) || !(beta > 0.0 && beta <= 1.0)) return -1;
+    if (!valid_variant(variant) || !(beta > 0.0 && beta <= 1.0) || gmode == 2) return -1;
     const double hs = 1e-30;
     for (int p = 0; p < n; ++p) {
         double complex fc[9], oc[9];
@@ -373,7 +377,7 @@ int kbco_adjoint(int nx, int ny, int variant, double beta, int gmode, double gfi
                  double* J, double* gux, double* guy, double* gbeta)
 {
     if (nx < 1 || ny < 1 || nsteps < 0 || !valid_variant(variant) ||
-        !(beta > 0.0 && beta <= 1.0) || (objective != 0 && objective != 1))
+        !(beta > 0.0 && beta <= 1.0) || (objective != 0 && objective != 1) || gmode == 2)
         return -1;
     const size_t np = (size_t)nx * ny, fs = 9 * np;
     double* states = malloc((size_t)(nsteps + 1) * fs * sizeof(double));

@@ -115,10 +115,13 @@ class Lattice:
             pass
 
     # -- configuration
-    def set_gamma(self, gamma_fixed: float | None):
-        """None: entropic gamma (Eq. result21); a number: gamma fixed to it."""
+    def set_gamma(self, gamma_fixed):
+        """None: entropic gamma* (Eq. result21); "exact": root of Eq. result1;
+        a number: gamma fixed to it."""
         if gamma_fixed is None:
             capi.kbc_set_gamma_mode(self.h, KBC_GAMMA_ENTROPIC, 2.0)
+        elif gamma_fixed == "exact":
+            capi.kbc_set_gamma_mode(self.h, capi.KBC_GAMMA_EXACT, 2.0)
         else:
             capi.kbc_set_gamma_mode(self.h, KBC_GAMMA_FIXED, float(gamma_fixed))
 

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libkbc_gb300.so")
 
 KBC_LBGK, KBC_A, KBC_B, KBC_C, KBC_D = 0, 1, 2, 3, 4
 KBC_F64, KBC_F32_DEV, KBC_F16_DEV = 0, 1, 2
-KBC_GAMMA_ENTROPIC, KBC_GAMMA_FIXED = 0, 1
+KBC_GAMMA_ENTROPIC, KBC_GAMMA_FIXED, KBC_GAMMA_EXACT = 0, 1, 2
 KBC_OK, KBC_ERR_ARG, KBC_ERR_CUDA, KBC_ERR_NOMEM = 0, -1, -2, -3
 KBC_ERR_NONFINITE, KBC_ERR_TIMEOUT, KBC_ERR_STATE = -4, -5, -6
 KBC_DIAG_N = 10

@@ -171,7 +171,7 @@ StepArgs args_of(const kbc_ctx* h)
     a.plane = h->plane;
     a.cs.scale = h->f16_scale;
     a.cs.inv_scale = 1.0f / h->f16_scale;
-    const int fixed = (h->gamma_mode == KBC_GAMMA_FIXED) ? 1 : 0;
+    const int fixed = (h->gamma_mode == KBC_GAMMA_FIXED) ? 1 : (h->gamma_mode == KBC_GAMMA_EXACT ? 2 : 0);
     const double guard = (h->dtype == KBC_F64) ? 0.0 : h->guard;
     a.pf = make_params<float>(h->beta, fixed, h->gamma_fixed, guard);
     a.pd = make_params<double>(h->beta, fixed, h->gamma_fixed, guard);
@@ -246,6 +246,7 @@ static int step_into(kbc_handle h, const void* src, void* dst)
     L.variant = h->variant;
     L.rows = h->kernel != KBC_KERNEL_NODES && (h->nx % (32 * vec_width(h->dtype))) == 0;
     L.tma = h->kernel == KBC_KERNEL_BULK && h->dtype != KBC_F64 && (h->nx % kTmaTile) == 0;
+    L.all_f64 = h->gamma_mode == KBC_GAMMA_EXACT && h->variant != KBC_LBGK;
     L.stream = h->stream;
     L.num_sms = h->num_sms;
     const bool guard_on = h->dtype != KBC_F64 && h->variant != KBC_LBGK &&
@@ -456,7 +457,7 @@ int kbc_set_stream(kbc_handle h, void* stream)
 int kbc_set_gamma_mode(kbc_handle h, int mode, double gamma_fixed)
 {
     if (!h) return KBC_ERR_ARG;
-    if (mode != KBC_GAMMA_ENTROPIC && mode != KBC_GAMMA_FIXED)
+    if (mode != KBC_GAMMA_ENTROPIC && mode != KBC_GAMMA_FIXED && mode != KBC_GAMMA_EXACT)
         return fail(h, KBC_ERR_ARG, "bad gamma mode");
     if (mode == KBC_GAMMA_FIXED && !std::isfinite(gamma_fixed))
         return fail(h, KBC_ERR_ARG, "gamma must be finite");
@@ -703,6 +704,8 @@ int kbc_adjoint(kbc_handle h, const double* rho0, const double* u0, int nsteps, 
     if (nsteps < 0 || ckpt_every < 1) return fail(h, KBC_ERR_ARG, "nsteps >= 0, ckpt_every >= 1");
     if (objective != 0 && objective != 1) return fail(h, KBC_ERR_ARG, "objective must be 0 or 1");
     if (objective == 1 && !u_target) return fail(h, KBC_ERR_ARG, "objective 1 needs u_target");
+    if (h->gamma_mode == KBC_GAMMA_EXACT && h->variant != KBC_LBGK)
+        return fail(h, KBC_ERR_ARG, "the adjoint supports the entropic and fixed gamma modes");
     const long long n = (long long)h->nx * h->ny;
     const size_t field = (size_t)9 * h->plane * h->elem;
     const size_t tsize = (h->dtype == KBC_F64) ? sizeof(double) : sizeof(float);

@@ -24,6 +24,8 @@
 // update f - 2 beta df (Eq. LBGKmirr) bit for bit.
 #pragma once
 
+#include <type_traits>
+
 #include "kbc_lattice.cuh"
 
 namespace kbc {
@@ -41,6 +43,7 @@ struct CollideParams {
     T gamma_fixed;
     T guard;           // threshold on rho <dh|dh>; <= 0 disables
     int fixed;         // 1: gamma = gamma_fixed
+    int exact;         // 1: gamma from the root of Eq. result1 (double arithmetic only)
 };
 
 template <typename T>
@@ -54,7 +57,8 @@ __host__ inline CollideParams<T> make_params(double beta, int fixed, double gamm
     p.ch_fixed = (T)(beta * (gamma_fixed - 2.0));
     p.gamma_fixed = (T)gamma_fixed;
     p.guard = (T)guard;
-    p.fixed = fixed;
+    p.fixed = fixed == 1 ? 1 : 0;
+    p.exact = fixed == 2 ? 1 : 0;
     return p;
 }
 
@@ -114,6 +118,36 @@ __device__ __forceinline__ void inv9(const T (&x)[9], T (&w)[9])
         inv = inv * x[k];
     }
     w[0] = inv;
+}
+
+// Root of the exact entropic condition Eq. result1,
+//   F(g) = sum_i dh_i ln(1 + ((1 - beta g) dh_i - (2 beta - 1) ds_i) / f^eq_i) = 0,
+// by Newton's method from gamma* (F is decreasing wherever every
+// post-collision population is positive: F'(g) = -beta sum dh_i^2 / f'_i).
+// Stops when the step is below 1e-13 |g|; keeps gamma* when an iterate leaves
+// that domain, F' is not negative, or 30 iterations pass.  w_i = rho / f^eq_i.
+__device__ __forceinline__ double exact_gamma(const double (&ds)[9], const double (&dh)[9],
+                                              const double (&w)[9], double rho, double beta,
+                                              double g0)
+{
+    const double irho = 1.0 / rho;
+    double g = g0;
+    for (int it = 0; it < 30; ++it) {
+        double F = 0.0, dF = 0.0;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const double q = w[i] * irho;  // 1 / f^eq_i
+            const double x = ((1.0 - beta * g) * dh[i] - (2.0 * beta - 1.0) * ds[i]) * q;
+            if (!(x > -1.0)) return g0;
+            F += dh[i] * log1p(x);
+            dF -= beta * dh[i] * dh[i] * q / (1.0 + x);
+        }
+        if (!(dF < 0.0)) return g0;
+        const double step = F / dF;
+        g -= step;
+        if (fabs(step) <= 1e-13 * fabs(g)) return g;
+    }
+    return g0;
 }
 
 // Returns gamma; rho_out receives rho (NaN/Inf flags a blown-up node);
@@ -235,6 +269,13 @@ __device__ __forceinline__ T collide(T (&d)[9], const CollideParams<T>& p, T& rh
                 const T R = ratio(sh, hh);
                 ch = p.one_m_2beta * (T(1) + R);             // beta (gamma - 2)
                 gamma = fmaT(-p.two_m_inv_beta, R, p.inv_beta);
+                if constexpr (std::is_same<T, double>::value) {
+                    if (p.exact) {
+                        const double beta = 0.5 * p.two_beta;
+                        gamma = exact_gamma(ds, dh, w, rho, beta, gamma);
+                        ch = beta * (gamma - 2.0);
+                    }
+                }
             } else {
                 // <dh|dh> = 0: dh = 0 and gamma multiplies nothing; report 2
                 ch = T(0);

@@ -247,6 +247,40 @@ step_nodes(const typename C::S* __restrict__ src, typename C::S* __restrict__ ds
     }
 }
 
+// ---------------------------------------------------------------- all-FP64 step
+//
+// One node per thread with the whole collision in double whatever the
+// storage; used for the exact-gamma mode (root of Eq. result1), whose Newton
+// iteration runs in double.
+template <int VAR, class C>
+__global__ void __launch_bounds__(256)
+step_nodes_f64(const typename C::S* __restrict__ src, typename C::S* __restrict__ dst, StepArgs a)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0 && a.fix_count) a.fix_count[a.fix_slot ^ 1] = 0;
+    const long long total = (long long)a.nx * a.ny;
+    CollideParams<double> p = a.pd;
+    p.guard = 0.0;
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < total;
+         n += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(n / a.nx), x = (int)(n - (long long)y * a.nx);
+        double f[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const int ai = i % 3 - 1, bi = i / 3 - 1;
+            int sx = x - ai, sy = y - bi;
+            sx = sx < 0 ? sx + a.nx : (sx >= a.nx ? sx - a.nx : sx);
+            sy = sy < 0 ? sy + a.ny : (sy >= a.ny ? sy - a.ny : sy);
+            f[i] = C::to_f64(src[(long long)i * a.plane + (long long)sy * a.nx + sx], i, a.cs);
+        }
+        double rho;
+        bool hit;
+        collide<VAR>(f, p, rho, hit);
+        if (!isfinite(rho)) *a.flag = 1;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) dst[(long long)i * a.plane + n] = C::from_f64(f[i], i, a.cs);
+    }
+}
+
 // ---------------------------------------------------------------- FP64 re-evaluation
 //
 // Recomputes, entirely in double, the nodes the step recorded (entropic

@@ -17,6 +17,7 @@ struct Launch {
     int variant;
     bool rows;      // vectorised row kernel (nx % (32 * kVec) == 0)
     bool tma;       // persistent bulk-copy kernel (nx % kTmaTile == 0, F32/F16)
+    bool all_f64;   // whole collision in double (exact-gamma mode)
     bool fixup;     // FP64 re-evaluation pass after the step
     cudaStream_t stream;
     int num_sms;
@@ -39,6 +40,12 @@ cudaError_t launch_step_v(const Launch& L)
     using S = typename C::S;
     const S* src = static_cast<const S*>(L.src);
     S* dst = static_cast<S*>(L.dst);
+    if (L.all_f64) {
+        const long long total = (long long)L.a.nx * L.a.ny;
+        step_nodes_f64<VAR, C><<<grid_for(total, kNodeBlock, L.num_sms, 16), kNodeBlock, 0,
+                                 L.stream>>>(src, dst, L.a);
+        return cudaGetLastError();
+    }
     if constexpr (!std::is_same<C, CodecF64>::value) {
         if (L.tma) {
             constexpr size_t smem = tma_smem_bytes<S, kTmaTile>();

@@ -389,3 +389,24 @@ def test_host_and_device_pointers_agree():
     assert np.array_equal(ra, h_rho) and np.array_equal(xa, h_u[0]) and np.array_equal(ya, h_u[1])
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("variant", ["A", "B", "C", "D"])
+def test_exact_gamma_mode_matches_oracle(variant, dtype):
+    """Exact-gamma mode (root of Eq. result1, FP64 Newton from gamma*): two
+    steps and the gamma statistics against the oracle's mode 2."""
+    nx, ny, beta = 256, 9, 0.96
+    g = representable(random_field(nx, ny, 31), dtype)
+    lat = Lattice(nx, ny, variant=variant, beta=beta, dtype=dtype)
+    lat.set_gamma("exact")
+    lat.set_populations(g)
+    d = lat.diagnostics()
+    lat.step(2)
+    got = lat.populations().cpu().numpy()
+    lat.close()
+    ref = O.step(g, OV[variant], beta, 2, gamma_mode=2)
+    assert np.max(np.abs(got - ref)) < (1e-13 if dtype == "f64" else 2e-6)
+    dref = O.diagnostics(g, OV[variant], beta, gamma_mode=2)
+    for k, name in ((5, "gamma_mean"), (6, "gamma_min"), (7, "gamma_max")):
+        assert d[name] == pytest.approx(dref[k], rel=1e-9)

@@ -595,3 +595,46 @@ def test_adjoint_matches_central_differences(objective):
         assert gy[yy, xx] == pytest.approx(fd, rel=1e-6, abs=1e-10)
     fd = (J_of(ux, uy, beta + h) - J_of(ux, uy, beta - h)) / (2 * h)
     assert gb == pytest.approx(fd, rel=1e-6, abs=1e-10)
+
+
+# ---------------------------------------------------------------- exact stabiliser
+
+
+@pytest.mark.parametrize("variant", KBC)
+def test_exact_gamma_is_the_root_of_the_entropic_condition(variant):
+    """gamma mode 2 returns the root of Eq. result1 (found independently with
+    brentq) and that root maximises the relative entropy
+    -sum f' ln(f'/f^eq) of the post-collision state over gamma (the condition
+    is beta times the derivative of that entropy)."""
+    beta = 0.93
+    f = random_states(25, 151 + variant, amp=0.03)
+    sp = O.split(variant, f)
+    _, gex = O.collide(variant, beta, f, gamma_mode=2)
+    _, gst = O.collide(variant, beta, f)
+    for n in range(f.shape[0]):
+        ds, dh, fe = sp["ds"][n], sp["dh"][n], sp["feq"][n]
+
+        def cond(x):
+            return np.sum(dh * np.log1p(((1 - beta * x) * dh - (2 * beta - 1) * ds) / fe))
+
+        root = brentq(cond, gst[n] - 3.0, gst[n] + 3.0, xtol=1e-15)
+        assert gex[n] == pytest.approx(root, rel=1e-11, abs=1e-11)
+
+        def neg_rel_entropy(g):
+            fp = fe + (1 - 2 * beta) * ds + (1 - beta * g) * dh
+            return np.sum(fp * np.log(fp / fe))
+
+        res = minimize_scalar(neg_rel_entropy, bracket=(gst[n] - 1, gst[n], gst[n] + 1),
+                              tol=1e-12)
+        assert gex[n] == pytest.approx(res.x, rel=1e-5, abs=1e-5)
+
+
+def test_exact_gamma_limits():
+    """At equilibrium the exact mode leaves the state unchanged (whatever
+    gamma the rounding-level dh yields); the exact mode is rejected by the
+    derivative routines."""
+    fe = O.feq([1.0], [0.02], [0.01])
+    out, _ = O.collide(O.B, 0.9, fe, gamma_mode=2)
+    assert np.allclose(out, fe, rtol=1e-15, atol=0)
+    with pytest.raises(ValueError):
+        O.collide_jacobian(O.B, 0.9, fe, gamma_mode=2)
