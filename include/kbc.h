@@ -81,8 +81,9 @@ enum kbc_status {
     KBC_ERR_STATE = -6      /* call out of order (e.g. step before init)      */
 };
 
-/* Number of doubles written by kbc_diagnostics. */
+/* Number of doubles written by kbc_diagnostics and kbc_diagnostics_ext. */
 #define KBC_DIAG_N 10
+#define KBC_DIAG_EXT_N 4
 
 /* Device allocator hook: returns a device pointer of at least `bytes` bytes
  * (256-byte aligned) or NULL; `stream` is the handle's bound stream. */
@@ -184,6 +185,15 @@ int kbc_moments(kbc_handle h, double* rho, double* u);
  *       performs (2 for LBGK)
  *   [8] spatial std of |u|^2/2   [9] spatial std of w^2/2 */
 int kbc_diagnostics(kbc_handle h, double* out);
+
+/* Further diagnostics of the paper's turbulence figures (FP64 device
+ * reductions), out[KBC_DIAG_EXT_N] on the host:
+ *   [0] palinstrophy P = mean |grad w|^2 / 2 (w as in kbc_diagnostics, its
+ *       gradient by periodic central differences)  [1] spatial std of
+ *       |grad w|^2 / 2
+ *   [2] mean entropy density s = -sum_i f_i ln(f_i / W_i) (Eq. S)
+ *   [3] spatial std of s */
+int kbc_diagnostics_ext(kbc_handle h, double* out);
 
 /* Diagnostics of a caller-owned population field without any device
  * allocation.  The paper has no counterpart to this call.

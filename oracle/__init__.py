@@ -67,6 +67,7 @@ def lib():
                 "kbco_step": (i, [i, i, i, db, i, db, i, d, d, d, i]),
                 "kbco_macro": (None, [i, i, d, d, d, d]),
                 "kbco_diagnostics": (i, [i, i, i, db, i, db, d, d]),
+                "kbco_diagnostics_ext": (i, [i, i, d, d]),
                 "kbco_adjoint": (i, [i, i, i, db, i, db, d, d, d, i, i, d, d, d, d, d, d]),
             }
             for name, (res, args) in sig.items():
@@ -221,6 +222,19 @@ def diagnostics(g, variant: int, beta: float, gamma_mode: int = 0,
     rc = lib().kbco_diagnostics(nx, ny, variant, float(beta), int(gamma_mode),
                                 float(gamma_fixed), _p(g), _p(out))
     if rc != 0:
+        raise ValueError("bad arguments")
+    return out
+
+
+DIAG_EXT_NAMES = ("P", "P_std", "S", "S_std")
+
+
+def diagnostics_ext(g) -> np.ndarray:
+    """palinstrophy (mean, std) and entropy density of Eq. S (mean, std)."""
+    g = _f64(g)
+    _, ny, nx = g.shape
+    out = np.empty(4)
+    if lib().kbco_diagnostics_ext(nx, ny, _p(g), _p(out)) != 0:
         raise ValueError("bad arguments")
     return out
 

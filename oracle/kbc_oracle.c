@@ -346,6 +346,53 @@ int kbco_diagnostics(int nx, int ny, int variant, double beta, int gmode,
     return 0;
 }
 
+/*
+ * Further diagnostics of the paper's turbulence figures, in this order:
+ *   [0] palinstrophy P = mean |grad w|^2 / 2, with w = d_x u_y - d_y u_x and
+ *       both derivatives by periodic central differences
+ *   [1] spatial std of |grad w|^2 / 2
+ *   [2] mean entropy density -sum_i f_i ln(f_i / W_i) (Eq. S)
+ *   [3] spatial std of the entropy density
+ */
+int kbco_diagnostics_ext(int nx, int ny, const double* g, double* out)
+{
+    if (nx < 1 || ny < 1) return -1;
+    const size_t np = (size_t)nx * ny;
+    double* rho = malloc(np * sizeof(double));
+    double* ux = malloc(np * sizeof(double));
+    double* uy = malloc(np * sizeof(double));
+    double* w = malloc(np * sizeof(double));
+    if (!rho || !ux || !uy || !w) { free(rho); free(ux); free(uy); free(w); return -2; }
+    kbco_macro(nx, ny, g, rho, ux, uy);
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x)
+            w[(size_t)y * nx + x] =
+                0.5 * (uy[(size_t)y * nx + wrap(x + 1, nx)] - uy[(size_t)y * nx + wrap(x - 1, nx)])
+              - 0.5 * (ux[wrap(y + 1, ny) * nx + x] - ux[wrap(y - 1, ny) * nx + x]);
+    double p = 0, p2 = 0, e = 0, e2 = 0;
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            const size_t c = (size_t)y * nx + x;
+            const double wx = 0.5 * (w[(size_t)y * nx + wrap(x + 1, nx)] - w[(size_t)y * nx + wrap(x - 1, nx)]);
+            const double wy = 0.5 * (w[wrap(y + 1, ny) * nx + x] - w[wrap(y - 1, ny) * nx + x]);
+            const double pp = 0.5 * (wx * wx + wy * wy);
+            p += pp; p2 += pp * pp;
+            double s = 0.0;
+            for (int i = 0; i < 9; ++i) {
+                const double f = g[i * np + c];
+                s -= f * log(f / kbco_W(i));
+            }
+            e += s; e2 += s * s;
+        }
+    const double inv = 1.0 / (double)np;
+    out[0] = p * inv;
+    out[1] = sqrt(fmax(p2 * inv - (p * inv) * (p * inv), 0.0));
+    out[2] = e * inv;
+    out[3] = sqrt(fmax(e2 * inv - (e * inv) * (e * inv), 0.0));
+    free(rho); free(ux); free(uy); free(w);
+    return 0;
+}
+
 /* ====================================================================== */
 /* Adjoint (discrete reverse sweep; complex-step local derivatives).        */
 /* ====================================================================== */

@@ -24,6 +24,7 @@ VARIANTS = {"lbgk": KBC_LBGK, "A": KBC_A, "B": KBC_B, "C": KBC_C, "D": KBC_D}
 DTYPES = {"f64": KBC_F64, "f32": KBC_F32_DEV, "f16": KBC_F16_DEV}
 DIAG_NAMES = ("mass", "px", "py", "E", "Z", "gamma_mean", "gamma_min", "gamma_max",
               "E_std", "Z_std")
+DIAG_EXT_NAMES = ("P", "P_std", "S", "S_std")
 
 
 def beta_from_viscosity(nu: float) -> float:
@@ -221,6 +222,15 @@ class Lattice:
         out = np.zeros(capi.KBC_DIAG_N)
         capi.kbc_diagnostics(self.h, out)
         return dict(zip(DIAG_NAMES, out.tolist()))
+
+    def diagnostics_ext(self) -> dict:
+        """Palinstrophy and entropy density (mean and spatial std)."""
+        import numpy as np
+
+        self._bind_stream()
+        out = np.zeros(capi.KBC_DIAG_EXT_N)
+        capi.kbc_diagnostics_ext(self.h, out)
+        return dict(zip(DIAG_EXT_NAMES, out.tolist()))
 
     @property
     def bytes_per_update(self) -> float:

@@ -21,6 +21,7 @@ KBC_GAMMA_ENTROPIC, KBC_GAMMA_FIXED, KBC_GAMMA_EXACT = 0, 1, 2
 KBC_OK, KBC_ERR_ARG, KBC_ERR_CUDA, KBC_ERR_NOMEM = 0, -1, -2, -3
 KBC_ERR_NONFINITE, KBC_ERR_TIMEOUT, KBC_ERR_STATE = -4, -5, -6
 KBC_DIAG_N = 10
+KBC_DIAG_EXT_N = 4
 KBC_KERNEL_AUTO, KBC_KERNEL_ROWS, KBC_KERNEL_NODES, KBC_KERNEL_BULK = 0, 1, 2, 3
 
 STATUS_NAMES = {
@@ -53,6 +54,7 @@ SIGNATURES = {
     "kbc_probe": (_i, [_vp, _i, _vp, _vp]),
     "kbc_moments": (_i, [_vp, _vp, _vp]),
     "kbc_diagnostics": (_i, [_vp, _vp]),
+    "kbc_diagnostics_ext": (_i, [_vp, _vp]),
     "kbc_diagnostics_noalloc": (_i, [_i, _i, _i, _d, _vp, _vp, _vp]),
     "kbc_adjoint": (_i, [_vp, _vp, _vp, _i, _i, _i, _vp, ctypes.POINTER(_d), _vp,
                          ctypes.POINTER(_d)]),
@@ -190,6 +192,10 @@ def kbc_moments(h, rho, u):
 
 def kbc_diagnostics(h, out):
     return check(h, load().kbc_diagnostics(h, ptr(out)))
+
+
+def kbc_diagnostics_ext(h, out):
+    return check(h, load().kbc_diagnostics_ext(h, ptr(out)))
 
 
 def kbc_diagnostics_noalloc(nx: int, ny: int, variant: int, beta: float, f, out,

@@ -55,6 +55,35 @@ __global__ void diag_final(const double* __restrict__ part, int nblocks, double*
     }
 }
 
+__global__ void diag_ext_final(const double* __restrict__ part, int nblocks, double* __restrict__ out,
+                               long long total)
+{
+    __shared__ double sm[kDiagExtParts][kDiagBlock];
+    double acc[kDiagExtParts] = {0, 0, 0, 0};
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+#pragma unroll
+        for (int k = 0; k < kDiagExtParts; ++k) acc[k] += part[(long long)b * kDiagExtParts + k];
+    }
+#pragma unroll
+    for (int k = 0; k < kDiagExtParts; ++k) sm[k][threadIdx.x] = acc[k];
+    __syncthreads();
+    for (int s = kDiagBlock / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+#pragma unroll
+            for (int k = 0; k < kDiagExtParts; ++k) sm[k][threadIdx.x] += sm[k][threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double inv = 1.0 / (double)total;
+        const double p = sm[0][0] * inv, e = sm[2][0] * inv;
+        out[0] = p;
+        out[1] = sqrt(fmax(sm[1][0] * inv - p * p, 0.0));
+        out[2] = e;
+        out[3] = sqrt(fmax(sm[3][0] * inv - e * e, 0.0));
+    }
+}
+
 __global__ void sum_partials(const double* __restrict__ part, int n, double* __restrict__ out)
 {
     __shared__ double sm[256];
@@ -818,6 +847,24 @@ int kbc_adjoint(kbc_handle h, const double* rho0, const double* u0, int nsteps, 
     if (h->flag_host[0] & 2) return fail(h, KBC_ERR_TIMEOUT, "a device-side wait ran out");
     if (h->flag_host[0]) return fail(h, KBC_ERR_NONFINITE, "non-finite populations in the forward sweep");
     return KBC_OK;
+}
+
+int kbc_diagnostics_ext(kbc_handle h, double* out)
+{
+    int rc = check_h(h);
+    if (rc) return rc;
+    if (!out) return fail(h, KBC_ERR_ARG, "NULL output");
+    if (!h->initialized) return fail(h, KBC_ERR_STATE, "field not initialised");
+    StepArgs a = args_of(h);
+    cudaError_t e = by_codec(h->dtype, [&](auto c) {
+        using C = decltype(c);
+        return launch_diag_ext<C>(h->buf[h->cur], h->diag_part, h->diag_nblocks, h->diag_out, a,
+                                  h->stream);
+    });
+    if (e != cudaSuccess) return cuda_fail(h, e, "diagnostics launch");
+    e = cudaMemcpyAsync(out, h->diag_out, KBC_DIAG_EXT_N * sizeof(double), cudaMemcpyDefault, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "diagnostics copy");
+    return wait_stream(h, 0);
 }
 
 int kbc_bytes_per_update(kbc_handle h, double* bytes)

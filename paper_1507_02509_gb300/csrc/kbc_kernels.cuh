@@ -528,6 +528,73 @@ diag_partial(const typename C::S* __restrict__ src, double* __restrict__ part, S
     }
 }
 
+// Palinstrophy and entropy density per block: part[block][4] = sums of
+// P = |grad w|^2 / 2 (w and its gradient by periodic central differences,
+// the same w as diag_partial), P^2, the entropy density of Eq. S,
+// s = -sum_i f_i ln(f_i / W_i) = -sum_i f_i log1p(d_i / W_i), and s^2.
+constexpr int kDiagExtParts = 4;
+
+template <class C>
+__device__ __forceinline__ double node_w(const typename C::S* __restrict__ src, int x, int y,
+                                         const StepArgs& a)
+{
+    auto idx = [&](int xx, int yy) -> long long {
+        xx = xx < 0 ? xx + a.nx : (xx >= a.nx ? xx - a.nx : xx);
+        yy = yy < 0 ? yy + a.ny : (yy >= a.ny ? yy - a.ny : yy);
+        return (long long)yy * a.nx + xx;
+    };
+    double r, uxp, uyp, uxm, uym, uxn, uyn, uxs, uys;
+    node_macro<C>(src, idx(x + 1, y), a, r, uxp, uyp);
+    node_macro<C>(src, idx(x - 1, y), a, r, uxm, uym);
+    node_macro<C>(src, idx(x, y + 1), a, r, uxn, uyn);
+    node_macro<C>(src, idx(x, y - 1), a, r, uxs, uys);
+    return 0.5 * (uyp - uym) - 0.5 * (uxn - uxs);
+}
+
+template <class C>
+__global__ void __launch_bounds__(kDiagBlock)
+diag_ext_partial(const typename C::S* __restrict__ src, double* __restrict__ part, StepArgs a)
+{
+    const long long total = (long long)a.nx * a.ny;
+    double acc[kDiagExtParts] = {0, 0, 0, 0};
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < total;
+         n += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(n / a.nx), x = (int)(n - (long long)y * a.nx);
+        const double wx = 0.5 * (node_w<C>(src, x + 1, y, a) - node_w<C>(src, x - 1, y, a));
+        const double wy = 0.5 * (node_w<C>(src, x, y + 1, a) - node_w<C>(src, x, y - 1, a));
+        const double pp = 0.5 * (wx * wx + wy * wy);
+        acc[0] += pp;
+        acc[1] += pp * pp;
+        double se = 0.0;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const double d = C::to_f64(src[(long long)i * a.plane + n], i, a.cs);
+            se -= (wgt(i) + d) * log1p(d * inv_wgt(i));
+        }
+        acc[2] += se;
+        acc[3] += se * se;
+    }
+    __shared__ double sm[kDiagExtParts][kDiagBlock];
+#pragma unroll
+    for (int k = 0; k < kDiagExtParts; ++k) sm[k][threadIdx.x] = acc[k];
+    __syncthreads();
+    for (int s = kDiagBlock / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+#pragma unroll
+            for (int k = 0; k < kDiagExtParts; ++k) sm[k][threadIdx.x] += sm[k][threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < kDiagExtParts; ++k) part[(long long)blockIdx.x * kDiagExtParts + k] = sm[k][0];
+    }
+}
+
+// Reduces part[nblocks][4] into out[4] = (mean P, std P, mean s, std s).
+__global__ void diag_ext_final(const double* __restrict__ part, int nblocks,
+                               double* __restrict__ out, long long total);
+
 // Reduces part[nblocks][10] (fixed order) into out[KBC_DIAG_N].
 __global__ void diag_final(const double* __restrict__ part, int nblocks, double* __restrict__ out,
                            long long total);

@@ -176,6 +176,15 @@ cudaError_t launch_diag(const void* src, double* part, int nblocks, double* out,
     return cudaGetLastError();
 }
 
+template <class C>
+cudaError_t launch_diag_ext(const void* src, double* part, int nblocks, double* out,
+                            const StepArgs& a, cudaStream_t s)
+{
+    diag_ext_partial<C><<<nblocks, kDiagBlock, 0, s>>>(static_cast<const typename C::S*>(src), part, a);
+    diag_ext_final<<<1, kDiagBlock, 0, s>>>(part, nblocks, out, (long long)a.nx * a.ny);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- adjoint
 
 inline int adj_blocks(long long total, int num_sms) { return grid_for(total, 256, num_sms, 8); }
@@ -237,6 +246,8 @@ cudaError_t launch_adj_grad_u0(const double* rho0, const double* ux0, const doub
                                                const StepArgs&, cudaStream_t);                \
     extern template cudaError_t launch_probe<C>(const void*, const long long*, int, double*,  \
                                                 int*, const StepArgs&, cudaStream_t, int);    \
+    extern template cudaError_t launch_diag_ext<C>(const void*, double*, int, double*,        \
+                                                   const StepArgs&, cudaStream_t);            \
     extern template cudaError_t launch_adj_step<C>(int, const void*, const void*, void*,      \
                                                    double*, int, const StepArgs&,             \
                                                    cudaStream_t);                             \
@@ -262,6 +273,8 @@ cudaError_t launch_adj_grad_u0(const double* rho0, const double* ux0, const doub
                                         const StepArgs&, cudaStream_t);                       \
     template cudaError_t launch_probe<C>(const void*, const long long*, int, double*, int*,   \
                                          const StepArgs&, cudaStream_t, int);                 \
+    template cudaError_t launch_diag_ext<C>(const void*, double*, int, double*,               \
+                                            const StepArgs&, cudaStream_t);                   \
     template cudaError_t launch_adj_step<C>(int, const void*, const void*, void*, double*,    \
                                             int, const StepArgs&, cudaStream_t);              \
     template cudaError_t launch_adj_objective<C>(const void*, const double*, const double*,   \

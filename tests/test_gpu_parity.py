@@ -410,3 +410,31 @@ def test_exact_gamma_mode_matches_oracle(variant, dtype):
     dref = O.diagnostics(g, OV[variant], beta, gamma_mode=2)
     for k, name in ((5, "gamma_mean"), (6, "gamma_min"), (7, "gamma_max")):
         assert d[name] == pytest.approx(dref[k], rel=1e-9)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "f16"])
+def test_diagnostics_ext_match_oracle(dtype):
+    """Palinstrophy and entropy density (mean, std) against the oracle on the
+    stored populations."""
+    nx, ny = 256, 33
+    g = representable(random_field(nx, ny, 17), dtype)
+    lat = Lattice(nx, ny, variant="B", beta=0.96, dtype=dtype)
+    lat.set_populations(g)
+    d = lat.diagnostics_ext()
+    lat.close()
+    ref = O.diagnostics_ext(g)
+    got = np.array([d[k] for k in O.DIAG_EXT_NAMES])
+    # stds come from one-pass variances: their resolution is sqrt(eps) |mean|
+    assert np.allclose(got[[0, 2]], ref[[0, 2]], rtol=1e-10, atol=0)
+    assert np.allclose(got[[1, 3]], ref[[1, 3]], rtol=1e-6, atol=3e-8 * np.abs(ref[[0, 2]]))
+
+
+def test_spectra_match_oracle():
+    from oracle import spectra as ospec
+    from paper_1507_02509_gb300.spectra import energy_spectrum
+
+    _, ux, uy = flows.turbulence(64, k0=6, urms=0.04, seed=12, kcut=24)
+    k, E, Z = energy_spectrum(torch.as_tensor(ux, device="cuda"), torch.as_tensor(uy, device="cuda"))
+    ko, Eo, Zo = ospec.energy_spectrum(ux, uy)
+    assert np.allclose(E.cpu().numpy(), Eo, rtol=1e-10, atol=1e-22)
+    assert np.allclose(Z.cpu().numpy(), Zo, rtol=1e-10, atol=1e-22)

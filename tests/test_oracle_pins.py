@@ -638,3 +638,39 @@ def test_exact_gamma_limits():
     assert np.allclose(out, fe, rtol=1e-15, atol=0)
     with pytest.raises(ValueError):
         O.collide_jacobian(O.B, 0.9, fe, gamma_mode=2)
+
+
+def test_diagnostics_ext_closed_forms():
+    """Palinstrophy of the discrete vortex with central differences is
+    u0^2 sin(k)^4; the entropy density of Eq. S vanishes at rest with unit
+    density and is -rho ln rho for a uniform density at rest."""
+    from paper_1507_02509_gb300 import flows
+
+    n, u0 = 32, 0.03
+    rho, ux, uy = flows.taylor_green(n, u0=u0)
+    k = 2 * math.pi / n
+    d = O.diagnostics_ext(O.init_feq(rho, ux, uy))
+    assert d[0] == pytest.approx(u0 * u0 * math.sin(k) ** 4, rel=1e-11)
+    rest = O.init_feq(np.ones((4, 6)), np.zeros((4, 6)), np.zeros((4, 6)))
+    d = O.diagnostics_ext(rest)
+    assert abs(d[2]) < 1e-16 and d[0] == 0.0
+    r0 = 1.3
+    d = O.diagnostics_ext(O.init_feq(np.full((4, 6), r0), np.zeros((4, 6)), np.zeros((4, 6))))
+    assert d[2] == pytest.approx(-r0 * math.log(r0), rel=1e-14)
+    assert d[3] < 3e-8  # one-pass variance: resolution sqrt(eps) |mean|
+
+
+def test_spectra_oracle_parseval_and_single_mode():
+    """sum_k E(k) equals mean |u|^2 / 2 (Parseval); the Taylor-Green vortex
+    with m modes puts all its energy in the shell round(sqrt(2) m)."""
+    from oracle import spectra
+    from paper_1507_02509_gb300 import flows
+
+    rho, ux, uy = flows.turbulence(32, k0=4, urms=0.05, seed=3, kcut=12)
+    k, E, Z = spectra.energy_spectrum(ux, uy)
+    assert E.sum() == pytest.approx(0.5 * np.mean(ux ** 2 + uy ** 2), rel=1e-12)
+    _, ux, uy = flows.taylor_green(32, u0=0.02, modes=3)
+    k, E, Z = spectra.energy_spectrum(ux, uy)
+    assert E[4] == pytest.approx(0.02 ** 2 / 4, rel=1e-12)
+    assert E.sum() - E[4] < 1e-20
+    assert Z[4] == pytest.approx((2 * math.pi * 4 / 32) ** 2 * E[4])
