@@ -62,16 +62,22 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
-STEP_KERNEL_SOURCES = ("kbc_lattice.cuh", "kbc_collide.cuh", "kbc_kernels.cuh", "kbc_launch.cuh")
-
-
 def kernel_source_hash() -> str:
-    """Hash of the sources that define the step kernel and its launch."""
-    h = hashlib.sha256()
+    """Hash of the code that defines the vector-row step kernel: the lattice
+    and collision headers, the kernel's own section of kbc_kernels.cuh and
+    its launch width."""
     csrc = os.path.join(ROOT, "paper_1507_02509_gb300", "csrc")
-    for name in STEP_KERNEL_SOURCES:
+    h = hashlib.sha256()
+    for name in ("kbc_lattice.cuh", "kbc_collide.cuh"):
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(name.encode() + f.read())
+    with open(os.path.join(csrc, "kbc_kernels.cuh")) as f:
+        text = f.read()
+    a = text.index("// ---------------------------------------------------------------- step, rows")
+    b = text.index("// ---------------------------------------------------------------- step, nodes")
+    h.update(text[a:b].encode())
+    with open(os.path.join(csrc, "kbc_launch.cuh")) as f:
+        h.update("".join(l for l in f if "kRowBlock" in l).encode())
     return h.hexdigest()[:16]
 
 
