@@ -120,10 +120,9 @@ __device__ __forceinline__ void record_fix_mask(unsigned hits, int n0, const Ste
 // stores per population plane.  Populations moving along x (a = +-1) need
 // the neighbour one element to the left/right: it comes from the adjacent
 // lane by a warp shuffle, and lanes 0 / 31 fetch it from memory (periodic
-// wrap at the row ends).  Requires nx % (32 NV) == 0.  The nbx * ny row
-// segments (nbx = ceil(nx / (BLOCK NV)) per row) are walked with a
-// grid-stride loop, so the grid may have one block per segment or fewer;
-// warps past the row end skip the segment as a whole.
+// wrap at the row ends).  Requires nx % (32 NV) == 0; a 1-D grid of
+// nbx * ny blocks, nbx = ceil(nx / (BLOCK NV)) blocks per row; warps past
+// the row end exit as a whole.
 template <int VAR, class C, int NV, int BLOCK>
 __global__ void __launch_bounds__(BLOCK)
 step_rows(const typename C::S* __restrict__ src, typename C::S* __restrict__ dst, StepArgs a,
@@ -131,90 +130,85 @@ step_rows(const typename C::S* __restrict__ src, typename C::S* __restrict__ dst
 {
     using S = typename C::S;
     using T = typename C::T;
+    const int y = blockIdx.x / nbx;
+    const int bx = blockIdx.x - y * nbx;
+    const int x0 = (bx * BLOCK + threadIdx.x) * NV;
     if (blockIdx.x == 0 && threadIdx.x == 0 && a.fix_count)
         a.fix_count[a.fix_slot ^ 1] = 0;  // free the other counter for the next step
+    if (x0 >= a.nx) return;               // whole warps only (nx % (32 NV) == 0)
     const int lane = threadIdx.x & 31;
-    const CollideParams<T>& p = params_of<T>(a);
-    const int nseg = nbx * a.ny;
-    bool bad = false;
-    // one row segment of BLOCK * NV nodes per iteration (a grid of nseg blocks
-    // does exactly one iteration each)
-    for (int seg = blockIdx.x; seg < nseg; seg += gridDim.x) {
-        const int y = seg / nbx;
-        const int bx = seg - y * nbx;
-        const int x0 = (bx * BLOCK + threadIdx.x) * NV;
-        if (x0 >= a.nx) continue;  // whole warps only (nx % (32 NV) == 0)
-        const int ym = (y == 0) ? a.ny - 1 : y - 1;
-        const int yp = (y == a.ny - 1) ? 0 : y + 1;
-        const int xl = (x0 == 0) ? a.nx - 1 : x0 - 1;
-        const int xr = (x0 + NV == a.nx) ? 0 : x0 + NV;
+    const int ym = (y == 0) ? a.ny - 1 : y - 1;
+    const int yp = (y == a.ny - 1) ? 0 : y + 1;
+    const int xl = (x0 == 0) ? a.nx - 1 : x0 - 1;
+    const int xr = (x0 + NV == a.nx) ? 0 : x0 + NV;
 
-        S raw[9][NV];
-        S edge[9];
+    S raw[9][NV];
+    S edge[9];
 #pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            const int ai = i % 3 - 1, bi = i / 3 - 1;
-            const int sy = (bi == 1) ? ym : (bi == -1 ? yp : y);   // source row y - b
-            const S* row = src + (long long)i * a.plane + (long long)sy * a.nx;
-            Vec<S, NV>::load(row + x0, raw[i]);
-            if (ai == 1) {
-                edge[i] = S(0);
-                if (lane == 0) edge[i] = __ldg(row + xl);
-            } else if (ai == -1) {
-                edge[i] = S(0);
-                if (lane == 31) edge[i] = __ldg(row + xr);
-            }
-        }
-        T f[NV][9];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            const int ai = i % 3 - 1;
-            if (ai == 0) {
-#pragma unroll
-                for (int k = 0; k < NV; ++k) f[k][i] = C::decode(raw[i][k], i, a.cs);
-            } else if (ai == 1) {  // source x - 1
-                S left = shfl_up1(raw[i][NV - 1]);
-                if (lane == 0) left = edge[i];
-                f[0][i] = C::decode(left, i, a.cs);
-#pragma unroll
-                for (int k = 1; k < NV; ++k) f[k][i] = C::decode(raw[i][k - 1], i, a.cs);
-            } else {               // source x + 1
-                S right = shfl_down1(raw[i][0]);
-                if (lane == 31) right = edge[i];
-#pragma unroll
-                for (int k = 0; k < NV - 1; ++k) f[k][i] = C::decode(raw[i][k + 1], i, a.cs);
-                f[NV - 1][i] = C::decode(right, i, a.cs);
-            }
-        }
-        unsigned hits = 0u;
-#pragma unroll
-        for (int k = 0; k < NV; ++k) {
-            T rho;
-            bool hit;
-            collide<VAR>(f[k], p, rho, hit);
-            bad |= !isfinite(rho);
-            hits |= (hit ? 1u : 0u) << k;
-        }
-        if constexpr (VAR != kLBGK) {
-            if (a.fix_list) record_fix_mask<NV>(hits, y * a.nx + x0, a);
-        }
-        const long long o = (long long)y * a.nx + x0;
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            if constexpr (std::is_same<C, CodecF16>::value && NV % 2 == 0) {
-                unsigned pk[NV / 2];
-#pragma unroll
-                for (int k = 0; k < NV; k += 2) pk[k / 2] = C::encode2(f[k][i], f[k + 1][i], i, a.cs);
-                Vec<unsigned, NV / 2>::store(reinterpret_cast<unsigned*>(dst + (long long)i * a.plane + o), pk);
-            } else {
-                S out[NV];
-#pragma unroll
-                for (int k = 0; k < NV; ++k) out[k] = C::encode(f[k][i], i, a.cs);
-                Vec<S, NV>::store(dst + (long long)i * a.plane + o, out);
-            }
+    for (int i = 0; i < 9; ++i) {
+        const int ai = i % 3 - 1, bi = i / 3 - 1;
+        const int sy = (bi == 1) ? ym : (bi == -1 ? yp : y);   // source row y - b
+        const S* row = src + (long long)i * a.plane + (long long)sy * a.nx;
+        Vec<S, NV>::load(row + x0, raw[i]);
+        if (ai == 1) {
+            edge[i] = S(0);
+            if (lane == 0) edge[i] = __ldg(row + xl);
+        } else if (ai == -1) {
+            edge[i] = S(0);
+            if (lane == 31) edge[i] = __ldg(row + xr);
         }
     }
+    T f[NV][9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const int ai = i % 3 - 1;
+        if (ai == 0) {
+#pragma unroll
+            for (int k = 0; k < NV; ++k) f[k][i] = C::decode(raw[i][k], i, a.cs);
+        } else if (ai == 1) {  // source x - 1
+            S left = shfl_up1(raw[i][NV - 1]);
+            if (lane == 0) left = edge[i];
+            f[0][i] = C::decode(left, i, a.cs);
+#pragma unroll
+            for (int k = 1; k < NV; ++k) f[k][i] = C::decode(raw[i][k - 1], i, a.cs);
+        } else {               // source x + 1
+            S right = shfl_down1(raw[i][0]);
+            if (lane == 31) right = edge[i];
+#pragma unroll
+            for (int k = 0; k < NV - 1; ++k) f[k][i] = C::decode(raw[i][k + 1], i, a.cs);
+            f[NV - 1][i] = C::decode(right, i, a.cs);
+        }
+    }
+    const CollideParams<T>& p = params_of<T>(a);
+    bool bad = false;
+    unsigned hits = 0u;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        T rho;
+        bool hit;
+        collide<VAR>(f[k], p, rho, hit);
+        bad |= !isfinite(rho);
+        hits |= (hit ? 1u : 0u) << k;
+    }
+    if constexpr (VAR != kLBGK) {
+        if (a.fix_list) record_fix_mask<NV>(hits, y * a.nx + x0, a);
+    }
     if (bad) *a.flag = 1;
+    const long long o = (long long)y * a.nx + x0;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        if constexpr (std::is_same<C, CodecF16>::value && NV % 2 == 0) {
+            unsigned pk[NV / 2];
+#pragma unroll
+            for (int k = 0; k < NV; k += 2) pk[k / 2] = C::encode2(f[k][i], f[k + 1][i], i, a.cs);
+            Vec<unsigned, NV / 2>::store(reinterpret_cast<unsigned*>(dst + (long long)i * a.plane + o), pk);
+        } else {
+            S out[NV];
+#pragma unroll
+            for (int k = 0; k < NV; ++k) out[k] = C::encode(f[k][i], i, a.cs);
+            Vec<S, NV>::store(dst + (long long)i * a.plane + o, out);
+        }
+    }
 }
 
 // ---------------------------------------------------------------- step, nodes
