@@ -122,9 +122,10 @@ int kbc_set_gamma_mode(kbc_handle h, int mode, double gamma_fixed);
  *                    choice measured on GB300 at 4096^2 and 16384^2);
  *   KBC_KERNEL_ROWS  the same choice, named explicitly;
  *   KBC_KERNEL_NODES the per-node kernel;
- *   KBC_KERNEL_BULK  the persistent kernel that stages each 1024-node row
- *                    tile in shared memory with bulk asynchronous copies
- *                    (F32/F16 with nx a multiple of 1024; otherwise as AUTO). */
+ *   KBC_KERNEL_BULK  the persistent, warp-specialised kernel that stages each
+ *                    512-node row tile in shared memory with bulk
+ *                    asynchronous copies issued by a producer warp (F32/F16
+ *                    with nx a multiple of 512; otherwise as AUTO). */
 enum kbc_kernel { KBC_KERNEL_AUTO = 0, KBC_KERNEL_ROWS = 1, KBC_KERNEL_NODES = 2, KBC_KERNEL_BULK = 3 };
 int kbc_set_kernel(kbc_handle h, int kernel);
 

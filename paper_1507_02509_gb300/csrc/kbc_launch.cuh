@@ -49,7 +49,7 @@ cudaError_t launch_step_v(const Launch& L)
     if constexpr (!std::is_same<C, CodecF64>::value) {
         if (L.tma) {
             constexpr size_t smem = tma_smem_bytes<S, kTmaTile>();
-            constexpr int threads = kTmaTile / C::kVec;
+            constexpr int threads = kTmaTile / C::kVec + 32;
             static int per_sm = 0;  // resident CTAs per SM, from the occupancy calculator
             if (per_sm == 0) {
                 cudaError_t e = cudaFuncSetAttribute(step_tma<VAR, C, kTmaTile>,

@@ -1,15 +1,18 @@
 // Persistent step kernel with bulk asynchronous copies (sm_100 family).
 //
 // Each CTA walks over row tiles of TX nodes (tile t covers row y, columns
-// [x0, x0 + TX)).  For every tile one thread issues, per population plane,
-// the bulk copy (cp.async.bulk, completion counted in bytes on an mbarrier)
-// of the source row segment the pull needs -- shifted by one column for
-// a = +-1, so the segment is widened by a 16-byte halo on the side it reads
-// from, with the periodic wrap at the row ends split into a second copy.
-// STAGES tiles are in flight while the CTA computes an earlier one from
-// shared memory; the collision is the same register-only collide() as the
-// other step kernels and results go straight to global memory with 16- or
-// 8-byte vector stores.
+// [x0, x0 + TX)).  A producer warp issues, per tile and population plane,
+// the bulk copy (cp.async.bulk, completion counted in bytes on the stage's
+// "full" mbarrier) of the source row segment the pull needs -- shifted by
+// one column for a = +-1, so the segment is widened by a 16-byte halo on the
+// side it reads from, with the periodic wrap at the row ends split into a
+// second copy.  Consumer warps wait on "full", take their operands into
+// registers, release the stage on its "empty" mbarrier (one arrival per
+// warp) and compute; the producer refills a stage once every consumer warp
+// has released it.  No CTA-wide barrier sits in the loop, so loads stay in
+// flight while the consumers compute.  The collision is the same
+// register-only collide() as the other step kernels, and results go straight
+// to global memory with 16- or 8-byte vector stores.
 //
 // Shared memory per stage: [9][TX + 2H] elements, H = 16 / sizeof(S); the
 // element for column x of the tile is at index x - x0 + H.
@@ -27,8 +30,8 @@
 
 namespace kbc {
 
-constexpr int kTmaStages = 3;
-constexpr int kTmaTile = 1024;          // nodes per tile
+constexpr int kTmaStages = 4;
+constexpr int kTmaTile = 512;           // nodes per tile
 constexpr unsigned kWaitLimit = 1u << 22;
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p)
@@ -39,6 +42,11 @@ __device__ __forceinline__ uint32_t smem_addr(const void* p)
 __device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count)
 {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes)
@@ -95,7 +103,7 @@ __host__ __device__ constexpr unsigned tma_stage_tx_bytes()
 template <class S, int TX>
 __host__ __device__ constexpr size_t tma_smem_bytes()
 {
-    return (size_t)kTmaStages * 9 * (TX + 2 * (16 / sizeof(S))) * sizeof(S) + kTmaStages * 8 + 64;
+    return (size_t)kTmaStages * 9 * (TX + 2 * (16 / sizeof(S))) * sizeof(S) + 2 * kTmaStages * 8 + 64;
 }
 
 // issue the copies of tile `t` into stage buffer `buf` (one thread)
@@ -149,10 +157,11 @@ __device__ __forceinline__ void lds_vec(const S* p, S (&v)[NV])
     for (int k = 0; k < NV; ++k) v[k] = u.s[k];
 }
 
-// Requires nx % TX == 0.  Grid: persistent, at most (tiles) CTAs of TX/NV
-// threads, dynamic shared memory tma_smem_bytes<S, TX>().
+// Requires nx % TX == 0.  Grid: persistent, at most (tiles) CTAs of
+// TX/NV + 32 threads (TX/NV consumers, one producer warp), dynamic shared
+// memory tma_smem_bytes<S, TX>().
 template <int VAR, class C, int TX>
-__global__ void __launch_bounds__(TX / C::kVec)
+__global__ void __launch_bounds__(TX / C::kVec + 32)
 step_tma(const typename C::S* __restrict__ src, typename C::S* __restrict__ dst, StepArgs a)
 {
     using S = typename C::S;
@@ -160,38 +169,63 @@ step_tma(const typename C::S* __restrict__ src, typename C::S* __restrict__ dst,
     constexpr int NV = C::kVec;
     constexpr int H = 16 / (int)sizeof(S);
     constexpr int ROW = TX + 2 * H;
+    constexpr int NCW = TX / NV / 32;  // consumer warps
     extern __shared__ __align__(128) unsigned char smem_raw[];
     S* stage_buf = reinterpret_cast<S*>(smem_raw);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + (size_t)kTmaStages * 9 * ROW * sizeof(S));
-    __shared__ int abort_flag;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + (size_t)kTmaStages * 9 * ROW * sizeof(S));
+    uint64_t* empty = full + kTmaStages;
+    __shared__ volatile int abort_flag;
 
     const int tiles_per_row = a.nx / TX;
     const int tiles = tiles_per_row * a.ny;
     const int first = blockIdx.x, stride = gridDim.x;
     const int my_tiles = first < tiles ? (tiles - 1 - first) / stride + 1 : 0;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (blockIdx.x == 0 && threadIdx.x == 0 && a.fix_count) a.fix_count[a.fix_slot ^ 1] = 0;
     if (threadIdx.x == 0) {
         abort_flag = 0;
-        for (int s = 0; s < kTmaStages; ++s) mbar_init(&bars[s], 1);
+        for (int s = 0; s < kTmaStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], NCW);
+        }
         fence_mbar_init();
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int k = 0; k < kTmaStages && k < my_tiles; ++k)
-            tma_issue<S, TX>(src, stage_buf + (size_t)k * 9 * ROW, &bars[k], first + k * stride,
-                             tiles_per_row, a);
+
+    if (warp == NCW) {
+        // ---------------------------------------------------------- producer
+        if (lane == 0) {
+            for (int k = 0; k < my_tiles; ++k) {
+                const int s = k % kTmaStages;
+                if (k >= kTmaStages) {
+                    const unsigned par = (unsigned)(((k / kTmaStages) - 1) & 1);
+                    if (!mbar_wait_bounded(&empty[s], par)) {
+                        abort_flag = 1;
+                        break;
+                    }
+                    fence_proxy_async();
+                }
+                if (abort_flag) break;
+                tma_issue<S, TX>(src, stage_buf + (size_t)s * 9 * ROW, &full[s],
+                                 first + k * stride, tiles_per_row, a);
+            }
+        }
+        return;
     }
+
+    // -------------------------------------------------------------- consumers
     const CollideParams<T>& p = params_of<T>(a);
-    const int lx = threadIdx.x * NV;
+    const int lx = (warp * 32 + lane) * NV;
     bool bad = false;
     int k = 0;
     for (; k < my_tiles; ++k) {
         const int s = k % kTmaStages;
         const unsigned parity = (unsigned)((k / kTmaStages) & 1);
-        if (!mbar_wait_bounded(&bars[s], parity)) abort_flag = 1;
-        __syncthreads();
-        if (abort_flag) break;
+        if (!mbar_wait_bounded(&full[s], parity)) {
+            abort_flag = 1;
+            break;
+        }
         const int t = first + k * stride;
         const int y = t / tiles_per_row;
         const int x0 = (t - y * tiles_per_row) * TX;
@@ -222,13 +256,9 @@ step_tma(const typename C::S* __restrict__ src, typename C::S* __restrict__ dst,
                 f[NV - 1][i] = C::decode(hi[0], i, a.cs);
             }
         }
-        // every thread has its operands in registers: the stage can be refilled
-        __syncthreads();
-        if (threadIdx.x == 0 && k + kTmaStages < my_tiles) {
-            fence_proxy_async();
-            tma_issue<S, TX>(src, stage_buf + (size_t)s * 9 * ROW, &bars[s],
-                             first + (k + kTmaStages) * stride, tiles_per_row, a);
-        }
+        // this warp's operands are in registers: release the stage
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
         unsigned hits = 0u;
 #pragma unroll
         for (int q = 0; q < NV; ++q) {
@@ -258,15 +288,13 @@ step_tma(const typename C::S* __restrict__ src, typename C::S* __restrict__ dst,
         }
     }
     if (bad) atomicOr(a.flag, 1);
-    if (abort_flag) {
-        if (threadIdx.x == 0) {
-            atomicOr(a.flag, 2);
-            // tiles k .. k + STAGES - 1 may still have copies in flight: wait for
-            // them (bounded) before this CTA's shared memory is released
+    if (k < my_tiles && lane == 0) {
+        // aborted: report, then wait (bounded) for the copies that may still be
+        // in flight into this CTA's shared memory before it is released
+        atomicOr(a.flag, 2);
+        if (warp == 0)
             for (int kk = k; kk < my_tiles && kk < k + kTmaStages; ++kk)
-                mbar_wait_bounded(&bars[kk % kTmaStages], (unsigned)((kk / kTmaStages) & 1));
-        }
-        __syncthreads();
+                mbar_wait_bounded(&full[kk % kTmaStages], (unsigned)((kk / kTmaStages) & 1));
     }
 }
 
