@@ -129,6 +129,16 @@ int kbc_set_gamma_mode(kbc_handle h, int mode, double gamma_fixed);
 enum kbc_kernel { KBC_KERNEL_AUTO = 0, KBC_KERNEL_ROWS = 1, KBC_KERNEL_NODES = 2, KBC_KERNEL_BULK = 3 };
 int kbc_set_kernel(kbc_handle h, int kernel);
 
+/* kbc_step replays a CUDA graph of `steps` consecutive steps (captured once
+ * per handle configuration on a private stream, then launched on the bound
+ * stream) for as many whole graphs as nsteps holds, and launches the rest
+ * one by one; this removes the per-launch overhead that dominates small
+ * grids.  Graphs give the same bits as individual launches.  steps must be
+ * even (the two population buffers return to their roles after an even
+ * count); 0 disables graphs.  Default 32.  Not used while the bound stream
+ * is itself being captured. */
+int kbc_set_graph_steps(kbc_handle h, int steps);
+
 /* Threshold on <dh|dh> (entropic scalar product of Sec. 4, computed with the
  * weights rho/f^eq_i) below which an F32/F16 node is recomputed entirely in
  * FP64 from its stored populations by a second pass.  0 disables the pass.

@@ -132,6 +132,10 @@ class Lattice:
              "nodes": capi.KBC_KERNEL_NODES, "bulk": capi.KBC_KERNEL_BULK}[kernel]
         capi.kbc_set_kernel(self.h, k)
 
+    def set_graph_steps(self, steps: int):
+        """Steps per CUDA graph replayed by step() (even; 0 = no graphs)."""
+        capi.kbc_set_graph_steps(self.h, steps)
+
     def set_guard(self, threshold: float):
         capi.kbc_set_guard(self.h, threshold)
 

@@ -42,6 +42,7 @@ SIGNATURES = {
     "kbc_set_stream": (_i, [_vp, _vp]),
     "kbc_set_gamma_mode": (_i, [_vp, _i, _d]),
     "kbc_set_kernel": (_i, [_vp, _i]),
+    "kbc_set_graph_steps": (_i, [_vp, _i]),
     "kbc_set_guard": (_i, [_vp, _d]),
     "kbc_guard_count": (_i, [_vp, ctypes.POINTER(ctypes.c_longlong)]),
     "kbc_set_f16_scale": (_i, [_vp, _d]),
@@ -142,6 +143,10 @@ def kbc_set_gamma_mode(h, mode: int, gamma_fixed: float = 2.0):
 
 def kbc_set_kernel(h, kernel: int):
     return check(h, load().kbc_set_kernel(h, int(kernel)))
+
+
+def kbc_set_graph_steps(h, steps: int):
+    return check(h, load().kbc_set_graph_steps(h, int(steps)))
 
 
 def kbc_set_guard(h, threshold: float):

@@ -138,6 +138,13 @@ struct kbc_ctx {
     size_t stage_bytes = 0;
     bool initialized = false;
     int kernel = KBC_KERNEL_AUTO;
+    // CUDA graphs of graph_steps (even) steps, one per (cur, fix_slot) parity,
+    // valid while config_version == graph_version[k]
+    int graph_steps = 32;
+    unsigned config_version = 1;
+    unsigned graph_version[4] = {0, 0, 0, 0};
+    cudaGraphExec_t graph[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaStream_t capture_stream = nullptr;
     cudaStream_t stream = nullptr;
     Allocator al;
     std::string err;
@@ -269,14 +276,15 @@ int check_h(kbc_ctx* h)
 
 // One step from src to dst with the handle's settings (guard pass and its
 // alternating counters included).
-static int step_into(kbc_handle h, const void* src, void* dst)
+static int step_into(kbc_handle h, const void* src, void* dst, cudaStream_t stream = nullptr,
+                     bool use_stream = false)
 {
     Launch L;
     L.variant = h->variant;
     L.rows = h->kernel != KBC_KERNEL_NODES && (h->nx % (32 * vec_width(h->dtype))) == 0;
     L.tma = h->kernel == KBC_KERNEL_BULK && h->dtype != KBC_F64 && (h->nx % kTmaTile) == 0;
     L.all_f64 = h->gamma_mode == KBC_GAMMA_EXACT && h->variant != KBC_LBGK;
-    L.stream = h->stream;
+    L.stream = use_stream ? stream : h->stream;
     L.num_sms = h->num_sms;
     const bool guard_on = h->dtype != KBC_F64 && h->variant != KBC_LBGK &&
                           h->gamma_mode == KBC_GAMMA_ENTROPIC && h->guard > 0.0 && h->fix;
@@ -292,6 +300,58 @@ static int step_into(kbc_handle h, const void* src, void* dst)
     if (e != cudaSuccess) return cuda_fail(h, e, "step launch");
     if (guard_on) h->fix_slot ^= 1;
     return KBC_OK;
+}
+
+static void drop_graphs(kbc_handle h)
+{
+    for (int k = 0; k < 4; ++k) {
+        if (h->graph[k]) cudaGraphExecDestroy(h->graph[k]);
+        h->graph[k] = nullptr;
+        h->graph_version[k] = 0;
+    }
+}
+
+// The instantiated graph of graph_steps steps starting from the current
+// (cur, fix_slot) parity, captured on a private stream; nullptr if capture
+// is not possible (the step then runs launch by launch).
+static cudaGraphExec_t step_graph(kbc_handle h)
+{
+    const int key = h->cur | (h->fix_slot << 1);
+    if (h->graph[key] && h->graph_version[key] == h->config_version) return h->graph[key];
+    if (h->graph[key]) {
+        cudaGraphExecDestroy(h->graph[key]);
+        h->graph[key] = nullptr;
+    }
+    if (!h->capture_stream &&
+        cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        h->capture_stream = nullptr;
+        return nullptr;
+    }
+    const int slot0 = h->fix_slot;
+    if (cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    int c = h->cur;
+    bool ok = true;
+    for (int s = 0; s < h->graph_steps && ok; ++s) {
+        ok = step_into(h, h->buf[c], h->buf[c ^ 1], h->capture_stream, true) == KBC_OK;
+        c ^= 1;
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(h->capture_stream, &g);
+    h->fix_slot = slot0;  // graph_steps is even: the replay returns to this parity
+    cudaGraphExec_t exec = nullptr;
+    if (ok && e == cudaSuccess && g && cudaGraphInstantiate(&exec, g, 0) == cudaSuccess) {
+        h->graph[key] = exec;
+        h->graph_version[key] = h->config_version;
+    } else {
+        exec = nullptr;
+    }
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return exec;
 }
 
 // device buffers owned by one call, released on every exit path
@@ -471,6 +531,8 @@ int kbc_destroy(kbc_handle h)
     dev_free(h, h->diag_out);
     dev_free(h, h->stage);
     if (h->flag_host) cudaFreeHost(h->flag_host);
+    drop_graphs(h);
+    if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
     cudaGetLastError();
     delete h;
     return KBC_OK;
@@ -492,6 +554,7 @@ int kbc_set_gamma_mode(kbc_handle h, int mode, double gamma_fixed)
         return fail(h, KBC_ERR_ARG, "gamma must be finite");
     h->gamma_mode = mode;
     h->gamma_fixed = gamma_fixed;
+    ++h->config_version;
     return KBC_OK;
 }
 
@@ -500,6 +563,16 @@ int kbc_set_kernel(kbc_handle h, int kernel)
     if (!h) return KBC_ERR_ARG;
     if (kernel < KBC_KERNEL_AUTO || kernel > KBC_KERNEL_BULK) return fail(h, KBC_ERR_ARG, "bad kernel");
     h->kernel = kernel;
+    ++h->config_version;
+    return KBC_OK;
+}
+
+int kbc_set_graph_steps(kbc_handle h, int steps)
+{
+    if (!h) return KBC_ERR_ARG;
+    if (steps < 0 || steps % 2 != 0) return fail(h, KBC_ERR_ARG, "graph steps must be even and >= 0");
+    h->graph_steps = steps;
+    drop_graphs(h);
     return KBC_OK;
 }
 
@@ -514,6 +587,7 @@ int kbc_set_guard(kbc_handle h, double threshold)
         if (e != cudaSuccess) return cuda_fail(h, e, "memset");
     }
     h->guard = threshold;
+    ++h->config_version;
     return KBC_OK;
 }
 
@@ -540,6 +614,7 @@ int kbc_set_f16_scale(kbc_handle h, double scale)
     if (!(scale > 0.0 && std::isfinite(scale))) return fail(h, KBC_ERR_ARG, "scale must be > 0");
     if (h->initialized) return fail(h, KBC_ERR_STATE, "set the scale before kbc_init");
     h->f16_scale = (float)scale;
+    ++h->config_version;
     return KBC_OK;
 }
 
@@ -596,7 +671,21 @@ int kbc_step(kbc_handle h, int nsteps)
     if (h->flag_host[0] & 2) return fail(h, KBC_ERR_TIMEOUT, "a device-side wait ran out");
     if (h->flag_host[0]) return fail(h, KBC_ERR_NONFINITE, "non-finite populations detected");
     if (nsteps == 0) return KBC_OK;
-    for (int s = 0; s < nsteps; ++s) {
+    int done = 0;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    const bool capturing = cudaStreamIsCapturing(h->stream, &cs) != cudaSuccess ||
+                           cs != cudaStreamCaptureStatusNone;
+    cudaGetLastError();
+    if (h->graph_steps > 0 && nsteps >= h->graph_steps && !capturing) {
+        cudaGraphExec_t g = step_graph(h);
+        if (g) {
+            for (; done + h->graph_steps <= nsteps; done += h->graph_steps) {
+                cudaError_t e = cudaGraphLaunch(g, h->stream);
+                if (e != cudaSuccess) return cuda_fail(h, e, "graph launch");
+            }
+        }
+    }
+    for (int s = done; s < nsteps; ++s) {
         rc = step_into(h, h->buf[h->cur], h->buf[h->cur ^ 1]);
         if (rc) return rc;
         h->cur ^= 1;
