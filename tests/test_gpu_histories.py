@@ -1,0 +1,32 @@
+"""Turbulence histories (shortened decaying-turbulence configuration): the
+FP64 device diagnostics of FP32 and FP16-storage runs track the FP64 run,
+mass is conserved, and KBC B's mean gamma sits near 1/beta as the zeroth- and
+first-order analysis of Sec. 4 predicts for model B."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_1507_02509_gb300 import runs  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def test_turbulence_histories_fp32_fp16_against_fp64():
+    n, steps, every = 1024, 600, 100
+    h = {dt: runs.turbulence_run(n=n, steps=steps, every=every, dtype=dt, seed=5)
+         for dt in ("f64", "f32", "f16")}
+    for dt in h:
+        assert h[dt]["blew_up"] is None
+    E64, Z64 = np.array(h["f64"]["E"]), np.array(h["f64"]["Z"])
+    for dt, tol in (("f32", 1e-5), ("f16", 2e-2)):
+        E, Z = np.array(h[dt]["E"]), np.array(h[dt]["Z"])
+        eE = np.max(np.abs(E - E64) / E64)
+        eZ = np.max(np.abs(Z - Z64) / Z64)
+        print(f"{dt}: energy history rel {eE:.2e}, enstrophy history rel {eZ:.2e}")
+        assert eE < tol and eZ < tol
+    m = np.array(h["f64"]["mass"])
+    assert np.max(np.abs(m - m[0])) <= 1e-12 * m[0]
+    beta = h["f64"]["beta"]
+    g = np.array(h["f64"]["gamma_mean"][1:])
+    assert np.all(np.abs(g - 1.0 / beta) < 0.1)
