@@ -185,26 +185,40 @@ def test_shear_layer_1024(dtype):
 
 def test_turbulence_4096_sampled():
     """Decaying turbulence 4096^2 (E(k) ~ k^4 exp(-2 (k/16)^2), u_rms = 0.03,
-    Re = 1e5), KBC B in f32 and f64: populations at 48 seeded nodes after 10
-    steps against the oracle run on periodic windows around each node."""
-    n, steps = 4096, 10
+    Re = 1e5), KBC B: populations and velocities at 28 seeded nodes (corners
+    included) after 100 steps against the oracle run on periodic windows
+    around each node (a node after n steps depends only on the (2n+1)^2 box
+    around it).  FP64 to 1e-12 in the populations, FP32 to 1e-5 and FP16 to
+    3e-3 in the relative velocity."""
+    n, steps = 4096, 100
     nu = n * 0.03 / 1e5
     beta = 1.0 / (6 * nu + 1)
     rho, ux, uy = flows.turbulence(n, k0=16, urms=0.03, seed=2024)
     rng = np.random.default_rng(1)
-    xy = [(int(x), int(y)) for x, y in zip(rng.integers(0, n, 48), rng.integers(0, n, 48))]
+    xy = [(int(x), int(y)) for x, y in zip(rng.integers(0, n, 24), rng.integers(0, n, 24))]
     xy += [(0, 0), (n - 1, n - 1), (0, n - 1), (n - 1, 0)]
     nodes = [y * n + x for x, y in xy]
     ref = windows(lambda xs, ys: O.init_feq(rho[np.ix_(ys, xs)], ux[np.ix_(ys, xs)],
                                             uy[np.ix_(ys, xs)]),
-                  n, n, xy, steps, O.B, beta)
-    for dtype, tol in (("f64", 1e-13), ("f32", 3e-6)):
+                  n, n, xy, steps, O.B, beta, nthreads=16)
+
+    def vel(f):
+        r = f.sum(1)
+        return (f @ O.VA.astype(float)) / r, (f @ O.VB.astype(float)) / r
+
+    rx, ry = vel(ref)
+    umax = max(np.abs(rx).max(), np.abs(ry).max())
+    for dtype, ftol, utol in (("f64", 1e-12, 1e-11), ("f32", None, 1e-5), ("f16", None, 3e-3)):
         lat = Lattice(n, n, variant="B", beta=beta, dtype=dtype)
         lat.init(rho, ux, uy).step(steps)
         got = lat.probe(nodes)
         lat.close()
-        err = np.max(np.abs(got - ref))
-        assert err < tol, (dtype, err)
+        gx, gy = vel(got)
+        uerr = max(np.abs(gx - rx).max(), np.abs(gy - ry).max()) / umax
+        print(f"turbulence 4096^2 {dtype}, 100 steps: sampled velocity rel error {uerr:.2e}")
+        if ftol is not None:
+            assert np.max(np.abs(got - ref)) < ftol, dtype
+        assert uerr < utol, (dtype, uerr)
 
 
 def test_full_size_16384_f32_sampled():
