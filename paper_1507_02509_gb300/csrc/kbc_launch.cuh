@@ -23,7 +23,7 @@ struct Launch {
     int num_sms;
 };
 
-constexpr int kRowBlock = 128;
+constexpr int kRowBlock = 64;
 constexpr int kNodeBlock = 256;
 
 inline int grid_for(long long total, int block, int num_sms, int per_sm)
