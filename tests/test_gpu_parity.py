@@ -498,3 +498,40 @@ def test_graph_replay_speeds_up_small_grids():
         lat.close()
     print(f"64^2, 2000 steps: launches {times[0] * 1e3:.1f} ms, graphs {times[32] * 1e3:.1f} ms")
     assert times[32] <= 1.1 * times[0]
+
+
+@pytest.mark.parametrize("scale", [1.0, 256.0, 1.0 / 16])
+def test_f16_scale(scale):
+    """The per-run scale S of the half encoding (f - W)/W * S: one step
+    against the oracle from the same stored input; the scale must be set
+    before initialisation."""
+    nx, ny = 256, 5
+    g = representable(random_field(nx, ny, 61), "f16", f16_scale=scale)
+    lat = Lattice(nx, ny, variant="B", beta=0.97, dtype="f16")
+    lat.set_f16_scale(scale)
+    lat.set_populations(g)
+    lat.step(1)
+    got = lat.populations().cpu().numpy()
+    with pytest.raises(KBCError) as e:
+        lat.set_f16_scale(2.0)
+    assert e.value.status == capi.KBC_ERR_STATE
+    lat.close()
+    ref = O.step(g, O.B, 0.97, 1)
+    assert np.max(np.abs(got - ref) / weights().reshape(9, 1, 1)) < 2e-3
+
+
+def test_guard_count_and_full_fp64_pass():
+    """With a guard far above every node's <dh|dh> each node is re-evaluated
+    in FP64 (guard count = node count) and the result is the FP64 collision
+    of the stored FP32 input, rounded once to float."""
+    nx, ny, beta = 256, 7, 0.98
+    g = representable(random_field(nx, ny, 71, amp=1e-4), "f32")
+    lat = Lattice(nx, ny, variant="B", beta=beta, dtype="f32")
+    lat.set_guard(1e3)
+    lat.set_populations(g)
+    lat.step(1)
+    assert lat.guard_count() == nx * ny
+    got = lat.populations().cpu().numpy()
+    lat.close()
+    ref = representable(O.step(g, O.B, beta, 1), "f32")
+    assert np.max(np.abs(got - ref)) <= 2 * np.finfo(np.float32).eps * 0.05
