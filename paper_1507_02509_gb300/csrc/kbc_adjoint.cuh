@@ -36,7 +36,7 @@ __device__ __forceinline__ void collide_adjoint(const T (&d)[9], const T (&lam)[
     const T jx = ((d[2] - d[0]) + (d[8] - d[6])) + (d[5] - d[3]);
     const T jy = ((d[6] - d[0]) + (d[8] - d[2])) + (d[7] - d[1]);
     const T rho = T(1) + drho;
-    const T irho = T(1) / rho;
+    const T irho = rcp_fast(rho);
     const T ux = jx * irho, uy = jy * irho;
     const T usq15 = T(1.5) * (ux * ux + uy * uy);
     T xi[9], P[9], df[9];
@@ -74,24 +74,27 @@ __device__ __forceinline__ void collide_adjoint(const T (&d)[9], const T (&lam)[
         const T e1x[3] = {cx - T(0.5), T(-2) * cx, cx + T(0.5)};
         const T e1y[3] = {cy - T(0.5), T(-2) * cy, cy + T(0.5)};
         const T e2[3] = {T(0.5), T(-1), T(0.5)};
-        T ds[9], dh[9], x[9], q[9];
+        T ds[9], dh[9], x[9], xi_inv[9], q[9];
         T sh = T(0), hh = T(0);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) x[i] = T(1) + P[i];
+        inv9(x, xi_inv);  // 1 / x_i
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             const int a = i % 3, b = i / 3;
             ds[i] = c20 * e2[a] * e0y[b] + c02 * e0x[a] * e2[b] + m11 * e1x[a] * e1y[b];
             dh[i] = df[i] - ds[i];
-            x[i] = T(1) + P[i];
-            q[i] = T(inv_wgt(i)) / x[i];
+            q[i] = T(inv_wgt(i)) * xi_inv[i];
             sh += ds[i] * dh[i] * q[i];
             hh += dh[i] * dh[i] * q[i];
         }
         T ch, R = T(0);
         const bool has_h = hh > T(0);
+        const T ihh = has_h ? rcp_fast(hh) : T(0);
         if (p.fixed) {
             ch = p.ch_fixed;
         } else if (has_h) {
-            R = sh / hh;
+            R = sh * ihh;
             ch = p.one_m_2beta * (T(1) + R);
         } else {
             ch = T(0);
@@ -111,14 +114,14 @@ __device__ __forceinline__ void collide_adjoint(const T (&d)[9], const T (&lam)[
             bb += chb * (T(-2) * (T(1) + R));
             Rb = chb * p.one_m_2beta;
         }
-        const T shb = has_h ? Rb / hh : T(0);
-        const T hhb = has_h ? -Rb * R / hh : T(0);
+        const T shb = Rb * ihh;
+        const T hhb = -Rb * R * ihh;
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             dsb[i] = shb * dh[i] * q[i];
             dhb[i] += shb * ds[i] * q[i] + T(2) * hhb * dh[i] * q[i];
             const T qb = shb * ds[i] * dh[i] + hhb * dh[i] * dh[i];
-            Pb[i] -= qb * q[i] / x[i];
+            Pb[i] -= qb * q[i] * xi_inv[i];
             dfb[i] += dhb[i];
             dsb[i] -= dhb[i];
         }
