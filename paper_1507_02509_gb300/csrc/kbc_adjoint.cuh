@@ -30,7 +30,6 @@ __device__ __forceinline__ void collide_adjoint(const T (&d)[9], const T (&lam)[
 {
     constexpr bool central = (VAR == kA || VAR == kB);
     const T two_beta = p.two_beta;
-    const T beta = T(0.5) * two_beta;
     // ---------------------------------------------------------------- forward
     const T drho = ((d[0] + d[8]) + (d[2] + d[6])) + ((d[1] + d[7]) + (d[3] + d[5])) + d[4];
     const T jx = ((d[2] - d[0]) + (d[8] - d[6])) + (d[5] - d[3]);
@@ -180,7 +179,6 @@ __device__ __forceinline__ void collide_adjoint(const T (&d)[9], const T (&lam)[
     drhob -= irhob * irho * irho;
 #pragma unroll
     for (int i = 0; i < 9; ++i) mu[i] += drhob + T(va(i)) * jxb + T(vb(i)) * jyb;
-    (void)beta;
     beta_bar = bb;
 }
 
