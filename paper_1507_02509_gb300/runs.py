@@ -55,14 +55,20 @@ def history(lat: Lattice, steps: int, every: int, ext: bool = True) -> dict:
 
 def turbulence_run(n: int = 4096, steps: int = 50000, every: int = 500, variant="B",
                    dtype="f32", k0: float = 16.0, urms: float = 0.03, reynolds: float = 1e5,
-                   seed: int = 0, f16_scale: float = 1.0, backend: str = "torch") -> dict:
-    """Decaying two-dimensional turbulence: E(k) ~ k^4 exp(-2 (k/k0)^2),
-    u_rms given, nu from Re = N sqrt(2E)/nu, equilibrium initialisation."""
+                   seed: int = 0, f16_scale: float = 1.0, backend: str = "torch",
+                   spectrum: str = "k4") -> dict:
+    """Decaying two-dimensional turbulence, equilibrium initialisation, nu from
+    Re = N sqrt(2E)/nu.  spectrum "k4": E(k) ~ k^4 exp(-2 (k/k0)^2); "paper":
+    E(k) ~ k^6 / (1 + (k/k0)^18), the narrow-band spectrum of the paper's
+    turbulence section."""
     from . import viscosity_for_reynolds
 
     nu = viscosity_for_reynolds(n, 0.5 * urms * urms, reynolds)
     beta = beta_from_viscosity(nu)
-    rho, ux, uy = flows.turbulence(n, k0=k0, urms=urms, seed=seed, backend=backend)
+    spec = flows.spectrum_k4_gauss if spectrum == "k4" else flows.spectrum_paper
+    rho, ux, uy = flows.turbulence(n, k0=k0, urms=urms, seed=seed, backend=backend,
+                                   spectrum=spec,
+                                   kcut=None if spectrum == "k4" else min(n // 2 - 1, int(4 * k0)))
     lat = Lattice(n, n, variant=variant, beta=beta, dtype=dtype)
     if dtype == "f16":
         lat.set_f16_scale(f16_scale)

@@ -30,3 +30,27 @@ def test_turbulence_histories_fp32_fp16_against_fp64():
     beta = h["f64"]["beta"]
     g = np.array(h["f64"]["gamma_mean"][1:])
     assert np.all(np.abs(g - 1.0 / beta) < 0.1)
+
+
+def test_lbgk_breaks_down_where_kbc_survives():
+    """The under-resolved high-Reynolds case of the turbulence section:
+    N = 1024, Re = 1.6e6 with the energy of Table 3 (E0 = 1.209e-4, hence
+    nu = 9.95e-6 and beta = 0.99994) and the paper's narrow-band spectrum
+    (k0 = 30).  The paper reports that LBGK crashes there while the KBC
+    models run trouble-free; here LBGK turns non-finite (caught by the step's
+    canary, reported as KBC_ERR_NONFINITE) within the first 100 eddy
+    turnover times' worth of steps, and KBC B stays finite with conserved
+    mass."""
+    e0 = 1.209e-4
+    urms = (2 * e0) ** 0.5
+    common = dict(n=1024, steps=20000, every=2000, dtype="f32", k0=30.0, urms=urms,
+                  reynolds=1.6e6, seed=11, spectrum="paper")
+    lbgk = runs.turbulence_run(variant="lbgk", **common)
+    kbc = runs.turbulence_run(variant="B", **common)
+    print(f"LBGK non-finite by step {lbgk['blew_up']}; KBC B finite: {kbc['blew_up'] is None}, "
+          f"E {kbc['E'][0]:.4e} -> {kbc['E'][-1]:.4e}")
+    assert abs(kbc["nu"] - 9.952e-6) < 1e-8
+    assert lbgk["blew_up"] is not None
+    assert kbc["blew_up"] is None
+    m = np.array(kbc["mass"])
+    assert np.all(np.isfinite(kbc["E"])) and abs(m[-1] - m[0]) <= 1e-8 * m[0]
