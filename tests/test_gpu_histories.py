@@ -43,7 +43,8 @@ def test_lbgk_breaks_down_where_kbc_survives():
     mass."""
     e0 = 1.209e-4
     urms = (2 * e0) ** 0.5
-    common = dict(n=1024, steps=20000, every=2000, dtype="f32", k0=30.0, urms=urms,
+    # 100 eddy turnover times, t_e = 512 (Table 3), sampled every 5 t_e
+    common = dict(n=1024, steps=51200, every=2560, dtype="f32", k0=30.0, urms=urms,
                   reynolds=1.6e6, seed=11, spectrum="paper")
     lbgk = runs.turbulence_run(variant="lbgk", **common)
     kbc = runs.turbulence_run(variant="B", **common)
