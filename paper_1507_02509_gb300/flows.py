@@ -51,6 +51,24 @@ def taylor_green_decay_rate(nu: float, n: int, modes: int = 1) -> float:
     return 2.0 * nu * k * k
 
 
+def taylor_green_k1k2(n: int, u0: float, k1: int = 1, k2: int = 4, t: float = 0.0,
+                      nu: float = 0.0, rho0: float = 1.0):
+    """The vortex of the paper's Green-Taylor section on [0, 2 pi)^2 sampled on
+    an n x n grid (node x_i = 2 pi i / n): the curl of
+    (u0/k2) cos(k1 x) cos(k2 y) exp(-nu (k1^2 + k2^2) t), i.e.
+    u_x = -u0 cos(k1 x) sin(k2 y) e, u_y = u0 (k1/k2) sin(k1 x) cos(k2 y) e,
+    with nu and t in lattice units (wavenumbers 2 pi k / n per node).
+    Constant density rho0."""
+    x = 2.0 * math.pi * np.arange(n, dtype=np.float64)[None, :] / n
+    y = 2.0 * math.pi * np.arange(n, dtype=np.float64)[:, None] / n
+    kk = (2.0 * math.pi / n) ** 2 * (k1 * k1 + k2 * k2)
+    e = math.exp(-nu * kk * t)
+    ux = -u0 * np.cos(k1 * x) * np.sin(k2 * y) * e
+    uy = u0 * (k1 / k2) * np.sin(k1 * x) * np.cos(k2 * y) * e
+    rho = np.full((n, n), rho0)
+    return np.ascontiguousarray(rho), np.ascontiguousarray(ux), np.ascontiguousarray(uy)
+
+
 def shear_layer(n: int, u0: float = 0.04, kappa: float = 80.0, delta: float = 0.05,
                 rho0: float = 1.0):
     """Doubly periodic shear layer on an n x n grid.

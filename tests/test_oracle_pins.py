@@ -674,3 +674,22 @@ def test_spectra_oracle_parseval_and_single_mode():
     assert E[4] == pytest.approx(0.02 ** 2 / 4, rel=1e-12)
     assert E.sum() - E[4] < 1e-20
     assert Z[4] == pytest.approx((2 * math.pi * 4 / 32) ** 2 * E[4])
+
+
+def test_taylor_green_k1k2_is_divergence_free_curl():
+    """The paper's vortex: spectral divergence vanishes and the vorticity is
+    the Laplacian-scaled stream function, for k1 = 1, k2 = 4."""
+    from paper_1507_02509_gb300 import flows
+
+    n = 64
+    _, ux, uy = flows.taylor_green_k1k2(n, u0=0.03, k1=1, k2=4)
+    kx = 2 * np.pi * np.fft.fftfreq(n, d=1.0 / n) / n
+    KX, KY = np.meshgrid(kx, kx)
+    div = np.fft.ifft2(1j * KX * np.fft.fft2(ux) + 1j * KY * np.fft.fft2(uy)).real
+    assert np.max(np.abs(div)) < 1e-15
+    w = np.fft.ifft2(1j * KX * np.fft.fft2(uy) - 1j * KY * np.fft.fft2(ux)).real
+    x = 2 * np.pi * np.arange(n)[None, :] / n
+    y = 2 * np.pi * np.arange(n)[:, None] / n
+    k2l = (2 * np.pi / n) ** 2 * 17
+    psi = (0.03 / 4) * np.cos(x) * np.cos(4 * y) * (n / (2 * np.pi))
+    assert np.allclose(w, k2l * psi, atol=1e-15)
