@@ -52,20 +52,26 @@ def taylor_green_decay_rate(nu: float, n: int, modes: int = 1) -> float:
 
 
 def taylor_green_k1k2(n: int, u0: float, k1: int = 1, k2: int = 4, t: float = 0.0,
-                      nu: float = 0.0, rho0: float = 1.0):
+                      nu: float = 0.0, rho0: float = 1.0, pressure_rho: bool = False):
     """The vortex of the paper's Green-Taylor section on [0, 2 pi)^2 sampled on
     an n x n grid (node x_i = 2 pi i / n): the curl of
     (u0/k2) cos(k1 x) cos(k2 y) exp(-nu (k1^2 + k2^2) t), i.e.
     u_x = -u0 cos(k1 x) sin(k2 y) e, u_y = u0 (k1/k2) sin(k1 x) cos(k2 y) e,
     with nu and t in lattice units (wavenumbers 2 pi k / n per node).
-    Constant density rho0."""
+    Constant density rho0, or with ``pressure_rho`` the density that carries
+    the vortex's pressure p = -(rho0 u0^2 / 4) (cos 2 k1 x + (k1/k2)^2 cos 2 k2 y)
+    through p = cs^2 rho, cs^2 = 1/3."""
     x = 2.0 * math.pi * np.arange(n, dtype=np.float64)[None, :] / n
     y = 2.0 * math.pi * np.arange(n, dtype=np.float64)[:, None] / n
     kk = (2.0 * math.pi / n) ** 2 * (k1 * k1 + k2 * k2)
     e = math.exp(-nu * kk * t)
     ux = -u0 * np.cos(k1 * x) * np.sin(k2 * y) * e
     uy = u0 * (k1 / k2) * np.sin(k1 * x) * np.cos(k2 * y) * e
-    rho = np.full((n, n), rho0)
+    if pressure_rho:
+        p = -0.25 * rho0 * u0 * u0 * e * e * (np.cos(2 * k1 * x) + (k1 / k2) ** 2 * np.cos(2 * k2 * y))
+        rho = rho0 + 3.0 * p
+    else:
+        rho = np.full((n, n), rho0)
     return np.ascontiguousarray(rho), np.ascontiguousarray(ux), np.ascontiguousarray(uy)
 
 
