@@ -63,12 +63,12 @@ def load_peaks():
 
 
 def kernel_source_hash() -> str:
-    """Hash of the code that defines the vector-row step kernel: the lattice
-    and collision headers, the kernel's own section of kbc_kernels.cuh and
-    its launch width."""
+    """Hash of the code that defines the vector-row step kernel: the lattice,
+    lane and collision headers, the kernel's own section of kbc_kernels.cuh
+    and its launch width."""
     csrc = os.path.join(ROOT, "paper_1507_02509_gb300", "csrc")
     h = hashlib.sha256()
-    for name in ("kbc_lattice.cuh", "kbc_collide.cuh"):
+    for name in ("kbc_lattice.cuh", "kbc_lanes.cuh", "kbc_collide.cuh"):
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(name.encode() + f.read())
     with open(os.path.join(csrc, "kbc_kernels.cuh")) as f:

@@ -26,6 +26,7 @@
 
 #include <type_traits>
 
+#include "kbc_lanes.cuh"
 #include "kbc_lattice.cuh"
 
 namespace kbc {
@@ -72,38 +73,36 @@ template <typename T> __device__ __forceinline__ T ratio(T a, T b);
 template <> __device__ __forceinline__ float ratio<float>(float a, float b) { return __fdividef(a, b); }
 template <> __device__ __forceinline__ double ratio<double>(double a, double b) { return a / b; }
 
-// xi_i = v_i . u for a compile-time velocity (a, b)
-template <int A, int B, typename T>
-__device__ __forceinline__ T vdot(T ux, T uy)
-{
-    if constexpr (A == 0 && B == 0) return T(0);
-    else if constexpr (A == 0) return B > 0 ? uy : -uy;
-    else if constexpr (B == 0) return A > 0 ? ux : -ux;
-    else return (A > 0 ? ux : -ux) + (B > 0 ? uy : -uy);
-}
-
-// P_i = 3 xi + 4.5 xi^2 - 1.5 u^2, so that f^eq_i = W_i rho (1 + P_i) (Eq. Eq)
-template <int I, typename T>
-__device__ __forceinline__ T eq_poly(T ux, T uy, T usq15)
+// P_i = 3 xi + 4.5 xi^2 - 1.5 u^2 with xi = v_i . u, so that
+// f^eq_i = W_i rho (1 + P_i) (Eq. Eq).  Opposite velocities share one xi:
+// P(-xi) = xi (4.5 xi - 3) - 1.5 u^2, so no negated operand is formed.
+// sxy = ux + uy, dxy = ux - uy, nusq15 = -1.5 |u|^2.
+template <int I, class L>
+__device__ __forceinline__ L eq_poly(L ux, L uy, L sxy, L dxy, L nusq15)
 {
     constexpr int A = I % 3 - 1, B = I / 3 - 1;
     if constexpr (A == 0 && B == 0) {
-        return -usq15;
+        return nusq15;
     } else {
-        const T xi = vdot<A, B>(ux, uy);
-        return fmaT(xi, fmaT(T(4.5), xi, T(3)), -usq15);
+        constexpr int sgn = (A == 0) ? B : A;  // sign of v_i . u relative to xi below
+        const L xi = (A == 0) ? uy : (B == 0) ? ux : (A == B) ? sxy : dxy;
+        return fmaL(xi, fmaL(L(4.5), xi, L(3 * sgn)), nusq15);
     }
 }
 
 // df_i = d_i - (f^eq_i - W_i), with f^eq - W = W (rho - 1 + rho P)
-template <int I, typename T>
-__device__ __forceinline__ T neq(T d, T rho, T drho, T P)
+template <int I, class L>
+__device__ __forceinline__ L neq(L d, L rho, L drho, L P)
 {
-    return d - T(wgt(I)) * fmaT(rho, P, drho);
+    return fmaL(L(-wgt(I)), fmaL(rho, P, drho), d);
 }
 
 // Montgomery's simultaneous inversion: w_i = 1 / x_i for nine x_i with one
-// reciprocal and 24 multiplications.
+// reciprocal and 24 multiplications.  The weights enter gamma* only through
+// the ratio <ds|dh> / <dh|dh>, so the rounding of the single shared
+// reciprocal cancels there; nine independent approximate reciprocals do not
+// (measured: three times the FP32-FP64 divergence of a turbulent run and a
+// much noisier FP32 adjoint).
 template <typename T>
 __device__ __forceinline__ void inv9(const T (&x)[9], T (&w)[9])
 {
@@ -150,142 +149,183 @@ __device__ __forceinline__ double exact_gamma(const double (&ds)[9], const doubl
     return g0;
 }
 
-// Returns gamma; rho_out receives rho (NaN/Inf flags a blown-up node);
-// guard_hit is set when the entropic denominator falls to or below the guard.
+// Collision of one node in a lane type (Lf: float, Ld: double).  Returns
+// gamma; rho_out receives rho (NaN/Inf flags a blown-up node); guard_hits is
+// 1 when the entropic denominator falls to or below the guard.
 //
 // Only six non-equilibrium parts are formed from the equilibrium; the other
 // three follow from sum df = sum a df = sum b df = 0 (the collision
 // conserves rho and rho u).  The rounding of f^eq (about eps |f^eq - W|)
 // then never leaks into the conserved moments, where nothing would damp it.
-template <int VAR, typename T>
-__device__ __forceinline__ T collide(T (&d)[9], const CollideParams<T>& p, T& rho_out,
-                                     bool& guard_hit)
+template <int VAR, class L>
+__device__ __forceinline__ L collide(L (&d)[9], const CollideParams<typename L::S>& p, L& rho_out,
+                                     unsigned& guard_hits)
 {
-    const T drho = ((d[0] + d[8]) + (d[2] + d[6])) + ((d[1] + d[7]) + (d[3] + d[5])) + d[4];
-    const T jx = ((d[2] - d[0]) + (d[8] - d[6])) + (d[5] - d[3]);
-    const T jy = ((d[6] - d[0]) + (d[8] - d[2])) + (d[7] - d[1]);
-    const T rho = T(1) + drho;
+    // column sums (a = +1, -1, 0) and row sums (b = +1, -1)
+    const L cR = (d[2] + d[5]) + d[8], cL = (d[0] + d[3]) + d[6], cM = (d[1] + d[4]) + d[7];
+    const L rT = (d[6] + d[7]) + d[8], rB = (d[0] + d[1]) + d[2];
+    const L drho = (cR + cL) + cM;
+    const L jx = cR - cL, jy = rT - rB;
+    const L rho = L(1) + drho;
     rho_out = rho;
-    const T irho = rcp_fast(rho);
-    const T ux = jx * irho, uy = jy * irho;
-    const T usq15 = T(1.5) * fmaT(ux, ux, uy * uy);
+    const L irho = rcp_fast(rho);
+    const L ux = jx * irho, uy = jy * irho;
+    const L uxx = ux * ux, uyy = uy * uy;
+    const L nusq15 = L(-1.5) * (uxx + uyy);
+    const L sxy = ux + uy, dxy = ux - uy;
 
-    T P[9], df[9];
-    P[0] = eq_poly<0>(ux, uy, usq15);
-    P[1] = eq_poly<1>(ux, uy, usq15);
-    P[2] = eq_poly<2>(ux, uy, usq15);
-    P[3] = eq_poly<3>(ux, uy, usq15);
-    P[6] = eq_poly<6>(ux, uy, usq15);
-    P[8] = eq_poly<8>(ux, uy, usq15);
+    L P[9], df[9];
+    P[0] = eq_poly<0>(ux, uy, sxy, dxy, nusq15);
+    P[1] = eq_poly<1>(ux, uy, sxy, dxy, nusq15);
+    P[2] = eq_poly<2>(ux, uy, sxy, dxy, nusq15);
+    P[3] = eq_poly<3>(ux, uy, sxy, dxy, nusq15);
+    P[6] = eq_poly<6>(ux, uy, sxy, dxy, nusq15);
+    P[8] = eq_poly<8>(ux, uy, sxy, dxy, nusq15);
     df[0] = neq<0>(d[0], rho, drho, P[0]);
     df[1] = neq<1>(d[1], rho, drho, P[1]);
     df[2] = neq<2>(d[2], rho, drho, P[2]);
     df[3] = neq<3>(d[3], rho, drho, P[3]);
     df[6] = neq<6>(d[6], rho, drho, P[6]);
     df[8] = neq<8>(d[8], rho, drho, P[8]);
-    df[5] = (df[3] - (df[2] + df[8])) + (df[0] + df[6]);
-    df[7] = (df[1] - (df[6] + df[8])) + (df[0] + df[2]);
-    df[4] = -(((df[0] + df[8]) + (df[2] + df[6])) + ((df[1] + df[7]) + (df[3] + df[5])));
+    df[5] = (df[3] - (df[2] + df[8])) + (df[0] + df[6]);  // sum a df = 0
+    df[7] = (df[1] - (df[6] + df[8])) + (df[0] + df[2]);  // sum b df = 0
+    // second moments of df; df carries no mass or momentum, so its central
+    // and natural second moments coincide (see header)
+    const L s08 = df[0] + df[8], s26 = df[2] + df[6];
+    const L corner = s08 + s26, s17 = df[1] + df[7];
+    const L m20 = corner + (df[3] + df[5]);
+    const L m02 = corner + s17;
+    df[4] = -(m20 + s17);                                 // sum df = 0
 
+    const L n2b(-p.two_beta);
     if constexpr (VAR == kLBGK) {
-        guard_hit = false;
+        guard_hits = 0u;
 #pragma unroll
-        for (int i = 0; i < 9; ++i) d[i] = fmaT(-p.two_beta, df[i], d[i]);
-        return T(2);
+        for (int i = 0; i < 9; ++i) d[i] = fmaL(n2b, df[i], d[i]);
+        return L(2);
     } else {
-        // second moments of df (natural = central, see header)
-        const T corner = (df[0] + df[2]) + (df[6] + df[8]);
-        const T m20 = corner + (df[3] + df[5]);
-        const T m02 = corner + (df[1] + df[7]);
-        const T m11 = (df[0] + df[8]) - (df[2] + df[6]);
-        // coefficients of E20, E02, E11 in ds: A/C carry T, N, Pi (all three
-        // second moments); B/D carry N and Pi only, i.e. the traceless part
-        // (m20 - m02)/2 (E20 - E02)
-        T c20, c02;
+        const L m11 = s08 - s26;
+        // ds = hc20 (2 E20) + hc02 (2 E02) + m11 E11 with hc = half the
+        // coefficient: A/C carry T, N, Pi (c20 = m20, c02 = m02); B/D carry N
+        // and Pi only, the traceless part c20 = -c02 = (m20 - m02)/2
+        L hc20, hc02;
         if constexpr (VAR == kA || VAR == kC) {
-            c20 = m20;
-            c02 = m02;
+            hc20 = L(0.5) * m20;
+            hc02 = L(0.5) * m02;
         } else {
-            c20 = T(0.5) * (m20 - m02);
-            c02 = -c20;
+            hc20 = L(0.25) * (m20 - m02);
+            hc02 = -hc20;
         }
-        T ds[9];
+        L ds[9];
         if constexpr (VAR == kA || VAR == kB) {
             // 1-D dual vectors about c: e0(c) = (c(c-1)/2, 1-c^2, c(c+1)/2),
-            // e1(c) = (c-1/2, -2c, c+1/2), e2 = (1/2, -1, 1/2)
-            const T hx = T(0.5) * ux, hy = T(0.5) * uy;
-            const T e0x[3] = {fmaT(hx, ux, -hx), fmaT(-ux, ux, T(1)), fmaT(hx, ux, hx)};
-            const T e0y[3] = {fmaT(hy, uy, -hy), fmaT(-uy, uy, T(1)), fmaT(hy, uy, hy)};
-            const T e1x[3] = {ux - T(0.5), T(-2) * ux, ux + T(0.5)};
-            const T e1y[3] = {uy - T(0.5), T(-2) * uy, uy + T(0.5)};
+            // e1(c) = (c-1/2, -2c, c+1/2), e2 = (1/2, -1, 1/2), and
             // ds_(a,b) = c20 e2[a] e0y[b] + c02 e0x[a] e2[b] + m11 e1x[a] e1y[b]
-            T Ab[3], Ba[3], Ca[3];
+            const L qx = L(0.5) * uxx, hx = L(0.5) * ux;
+            const L qy = L(0.5) * uyy, hy = L(0.5) * uy;
+            const L e0x[3] = {qx - hx, L(1) - uxx, qx + hx};
+            const L e0y[3] = {qy - hy, L(1) - uyy, qy + hy};
+            const L e1x[3] = {ux - L(0.5), L(-2) * ux, ux + L(0.5)};
+            const L e1y[3] = {uy - L(0.5), L(-2) * uy, uy + L(0.5)};
+            L Y[3], X[3], M[3];  // half c20 e0y, half c02 e0x, m11 e1x
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                Ab[k] = c20 * e0y[k];
-                Ba[k] = c02 * e0x[k];
-                Ca[k] = m11 * e1x[k];
+                Y[k] = hc20 * e0y[k];
+                X[k] = hc02 * e0x[k];
+                M[k] = m11 * e1x[k];
             }
+            // c20 e2[a] e0y[b] + c02 e0x[a] e2[b]: Y[b] + X[a] for a, b != 0,
+            // a factor -2 on the Y term when a = 0 and on the X term when b = 0
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
                 const int a = i % 3, b = i / 3;  // a, b in {0,1,2} <-> {-1,0,1}
-                const T ta = (a == 1) ? -Ab[b] : T(0.5) * Ab[b];
-                const T tb = (b == 1) ? -Ba[a] : T(0.5) * Ba[a];
-                ds[i] = fmaT(Ca[a], e1y[b], ta + tb);
+                L t;
+                if (a != 1 && b != 1) t = Y[b] + X[a];
+                else if (a == 1 && b != 1) t = fmaL(L(-2), Y[b], X[a]);
+                else if (a != 1) t = fmaL(L(-2), X[a], Y[b]);
+                else t = L(-2) * (Y[1] + X[1]);
+                ds[i] = fmaL(M[a], e1y[b], t);
             }
         } else {
             // natural basis (c = 0): e0 = (0,1,0), e1 = (-1/2, 0, 1/2)
-            const T q = T(0.25) * m11;
-            ds[4] = -(c20 + c02);
-            ds[3] = ds[5] = T(0.5) * c20;
-            ds[1] = ds[7] = T(0.5) * c02;
+            const L q = L(0.25) * m11;
+            ds[4] = L(-2) * (hc20 + hc02);
+            ds[3] = ds[5] = hc20;
+            ds[1] = ds[7] = hc02;
             ds[0] = ds[8] = q;
             ds[2] = ds[6] = -q;
         }
-        P[4] = eq_poly<4>(ux, uy, usq15);
-        P[5] = eq_poly<5>(ux, uy, usq15);
-        P[7] = eq_poly<7>(ux, uy, usq15);
-        T x[9], w[9];
+        P[4] = nusq15;
+        P[5] = eq_poly<5>(ux, uy, sxy, dxy, nusq15);
+        P[7] = eq_poly<7>(ux, uy, sxy, dxy, nusq15);
+        L x[9], w[9];
 #pragma unroll
-        for (int i = 0; i < 9; ++i) x[i] = fmaT(T(wgt(i)), P[i], T(wgt(i)));  // f^eq_i / rho
+        for (int i = 0; i < 9; ++i) x[i] = fmaL(L(wgt(i)), P[i], L(wgt(i)));  // f^eq_i / rho
         inv9(x, w);  // w_i = rho / f^eq_i
-        T dh[9];
-        T sh = T(0), hh = T(0);
+        L dh[9];
+        L sh, hh;
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             dh[i] = df[i] - ds[i];
-            const T t = dh[i] * w[i];
-            sh = fmaT(ds[i], t, sh);
-            hh = fmaT(dh[i], t, hh);
-        }
-        T ch, gamma;
-        guard_hit = false;
-        if (p.fixed) {
-            ch = p.ch_fixed;
-            gamma = p.gamma_fixed;
-        } else {
-            guard_hit = (p.guard > T(0)) && !(hh > p.guard);
-            if (hh > T(0)) {
-                const T R = ratio(sh, hh);
-                ch = p.one_m_2beta * (T(1) + R);             // beta (gamma - 2)
-                gamma = fmaT(-p.two_m_inv_beta, R, p.inv_beta);
-                if constexpr (std::is_same<T, double>::value) {
-                    if (p.exact) {
-                        const double beta = 0.5 * p.two_beta;
-                        gamma = exact_gamma(ds, dh, w, rho, beta, gamma);
-                        ch = beta * (gamma - 2.0);
-                    }
-                }
+            const L t = dh[i] * w[i];
+            if (i == 0) {
+                sh = ds[0] * t;
+                hh = dh[0] * t;
             } else {
-                // <dh|dh> = 0: dh = 0 and gamma multiplies nothing; report 2
-                ch = T(0);
-                gamma = T(2);
+                sh = fmaL(ds[i], t, sh);
+                hh = fmaL(dh[i], t, hh);
+            }
+        }
+        L nch, gamma;  // nch = -beta (gamma - 2)
+        guard_hits = 0u;
+        if (p.fixed) {
+            nch = L(-p.ch_fixed);
+            gamma = L(p.gamma_fixed);
+        } else {
+            if (p.guard > 0) guard_hits = ~gt_mask(hh, L(p.guard)) & ((1u << L::kLanes) - 1u);
+            // <dh|dh> = 0 means dh = 0: gamma multiplies nothing; report 2
+            const unsigned pos = gt_mask(hh, L(0));
+            const L R = ratio(sh, hh);
+            const L nb = L(-p.one_m_2beta);
+            nch = select(pos, fmaL(nb, R, nb), L(0));
+            gamma = select(pos, fmaL(L(-p.two_m_inv_beta), R, L(p.inv_beta)), L(2));
+            if constexpr (std::is_same<L, Ld>::value) {
+                if (p.exact && pos) {
+                    double dsd[9], dhd[9], wd[9];
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) {
+                        dsd[i] = ds[i].v;
+                        dhd[i] = dh[i].v;
+                        wd[i] = w[i].v;
+                    }
+                    const double beta = 0.5 * p.two_beta;
+                    gamma = Ld(exact_gamma(dsd, dhd, wd, rho.v, beta, gamma.v));
+                    nch = Ld(beta * (2.0 - gamma.v));
+                }
             }
         }
 #pragma unroll
-        for (int i = 0; i < 9; ++i) d[i] = fmaT(-ch, dh[i], fmaT(-p.two_beta, df[i], d[i]));
+        for (int i = 0; i < 9; ++i) d[i] = fmaL(nch, dh[i], fmaL(n2b, df[i], d[i]));
         return gamma;
     }
+}
+
+// One node in float or double (wraps the scalar into its lane type).
+template <int VAR, typename T>
+__device__ __forceinline__ T collide_node(T (&f)[9], const CollideParams<T>& p, T& rho, bool& hit)
+{
+    using L = typename LaneOf<T>::type;
+    L d[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) d[i] = L(f[i]);
+    L r;
+    unsigned h;
+    const L g = collide<VAR>(d, p, r, h);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) f[i] = d[i].v;
+    rho = r.v;
+    hit = (h & 1u) != 0u;
+    return g.v;
 }
 
 }  // namespace kbc

@@ -115,6 +115,24 @@ __device__ __forceinline__ void record_fix_mask(unsigned hits, int n0, const Ste
 }
 
 // ---------------------------------------------------------------- step, rows
+
+// Collides the NV nodes one thread holds.  Sets `bad` when a density is not
+// finite; bit k of the result marks a guard hit of node k.
+template <int VAR, typename T, int NV>
+__device__ __forceinline__ unsigned collide_vec(T (&f)[NV][9], const CollideParams<T>& p, bool& bad)
+{
+    unsigned hits = 0u;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        T rho;
+        bool hit;
+        collide_node<VAR>(f[k], p, rho, hit);
+        bad |= !isfinite(rho);
+        hits |= (hit ? 1u : 0u) << k;
+    }
+    return hits;
+}
+
 //
 // One thread updates NV consecutive nodes of one row with 16-byte loads and
 // stores per population plane.  Populations moving along x (a = +-1) need
@@ -124,7 +142,7 @@ __device__ __forceinline__ void record_fix_mask(unsigned hits, int n0, const Ste
 // nbx * ny blocks, nbx = ceil(nx / (BLOCK NV)) blocks per row; warps past
 // the row end exit as a whole.
 template <int VAR, class C, int NV, int BLOCK>
-__global__ void __launch_bounds__(BLOCK)
+__global__ void __launch_bounds__(BLOCK, C::kRowMinBlocks)
 step_rows(const typename C::S* __restrict__ src, typename C::S* __restrict__ dst, StepArgs a,
           int nbx)
 {
@@ -179,17 +197,8 @@ step_rows(const typename C::S* __restrict__ src, typename C::S* __restrict__ dst
             f[NV - 1][i] = C::decode(right, i, a.cs);
         }
     }
-    const CollideParams<T>& p = params_of<T>(a);
     bool bad = false;
-    unsigned hits = 0u;
-#pragma unroll
-    for (int k = 0; k < NV; ++k) {
-        T rho;
-        bool hit;
-        collide<VAR>(f[k], p, rho, hit);
-        bad |= !isfinite(rho);
-        hits |= (hit ? 1u : 0u) << k;
-    }
+    const unsigned hits = collide_vec<VAR>(f, params_of<T>(a), bad);
     if constexpr (VAR != kLBGK) {
         if (a.fix_list) record_fix_mask<NV>(hits, y * a.nx + x0, a);
     }
@@ -237,7 +246,7 @@ step_nodes(const typename C::S* __restrict__ src, typename C::S* __restrict__ ds
         }
         T rho;
         bool hit;
-        collide<VAR>(f, p, rho, hit);
+        collide_node<VAR>(f, p, rho, hit);
         if (!isfinite(rho)) *a.flag = 1;
         if constexpr (VAR != kLBGK) {
             if (a.fix_list) record_fix(hit, (int)n, a);
@@ -274,7 +283,7 @@ step_nodes_f64(const typename C::S* __restrict__ src, typename C::S* __restrict_
         }
         double rho;
         bool hit;
-        collide<VAR>(f, p, rho, hit);
+        collide_node<VAR>(f, p, rho, hit);
         if (!isfinite(rho)) *a.flag = 1;
 #pragma unroll
         for (int i = 0; i < 9; ++i) dst[(long long)i * a.plane + n] = C::from_f64(f[i], i, a.cs);
@@ -309,7 +318,7 @@ step_fixup(const typename C::S* __restrict__ src, typename C::S* __restrict__ ds
         q.guard = 0.0;
         double rho;
         bool hit;
-        collide<VAR>(f, q, rho, hit);
+        collide_node<VAR>(f, q, rho, hit);
 #pragma unroll
         for (int i = 0; i < 9; ++i) dst[(long long)i * a.plane + n] = C::from_f64(f[i], i, a.cs);
     }
@@ -504,7 +513,7 @@ diag_partial(const typename C::S* __restrict__ src, double* __restrict__ part, S
         }
         double rr;
         bool hit;
-        const double g = collide<VAR>(f, p, rr, hit);
+        const double g = collide_node<VAR>(f, p, rr, hit);
         acc[7] += g;
         acc[8] = fmin(acc[8], g);
         acc[9] = fmax(acc[9], g);

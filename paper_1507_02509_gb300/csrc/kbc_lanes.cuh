@@ -1,0 +1,65 @@
+// Arithmetic lanes of the collision.
+//
+// Every lane operation is one explicitly rounded IEEE operation (add, sub,
+// mul, fma with round-to-nearest) that the compiler never contracts into a
+// fused multiply-add or reorders.  Each kernel that inlines the collision
+// therefore evaluates exactly the operation sequence written in it, whatever
+// the surrounding code, and all step kernels produce identical bits.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <type_traits>
+
+namespace kbc {
+
+struct Lf {
+    using S = float;
+    static constexpr int kLanes = 1;
+    float v;
+    Lf() = default;
+    __device__ __forceinline__ explicit Lf(float x) : v(x) {}
+    __device__ __forceinline__ explicit Lf(double c) : v((float)c) {}
+    __device__ __forceinline__ explicit Lf(int c) : v((float)c) {}
+    __device__ __forceinline__ float get(int) const { return v; }
+};
+
+struct Ld {
+    using S = double;
+    static constexpr int kLanes = 1;
+    double v;
+    Ld() = default;
+    __device__ __forceinline__ explicit Ld(double x) : v(x) {}
+    __device__ __forceinline__ explicit Ld(int c) : v((double)c) {}
+    __device__ __forceinline__ double get(int) const { return v; }
+};
+
+// ---- Lf
+__device__ __forceinline__ Lf operator+(Lf a, Lf b) { return Lf(__fadd_rn(a.v, b.v)); }
+__device__ __forceinline__ Lf operator-(Lf a, Lf b) { return Lf(__fsub_rn(a.v, b.v)); }
+__device__ __forceinline__ Lf operator*(Lf a, Lf b) { return Lf(__fmul_rn(a.v, b.v)); }
+__device__ __forceinline__ Lf operator-(Lf a) { return Lf(-a.v); }
+__device__ __forceinline__ Lf fmaL(Lf a, Lf b, Lf c) { return Lf(__fmaf_rn(a.v, b.v, c.v)); }
+__device__ __forceinline__ Lf rcp_fast(Lf x) { return Lf(__fdividef(1.0f, x.v)); }
+__device__ __forceinline__ Lf ratio(Lf a, Lf b) { return Lf(__fdividef(a.v, b.v)); }
+__device__ __forceinline__ unsigned gt_mask(Lf a, Lf b) { return a.v > b.v ? 1u : 0u; }
+__device__ __forceinline__ unsigned finite_mask(Lf a) { return isfinite(a.v) ? 1u : 0u; }
+__device__ __forceinline__ Lf select(unsigned m, Lf a, Lf b) { return (m & 1u) ? a : b; }
+
+// ---- Ld
+__device__ __forceinline__ Ld operator+(Ld a, Ld b) { return Ld(__dadd_rn(a.v, b.v)); }
+__device__ __forceinline__ Ld operator-(Ld a, Ld b) { return Ld(__dsub_rn(a.v, b.v)); }
+__device__ __forceinline__ Ld operator*(Ld a, Ld b) { return Ld(__dmul_rn(a.v, b.v)); }
+__device__ __forceinline__ Ld operator-(Ld a) { return Ld(-a.v); }
+__device__ __forceinline__ Ld fmaL(Ld a, Ld b, Ld c) { return Ld(__fma_rn(a.v, b.v, c.v)); }
+__device__ __forceinline__ Ld rcp_fast(Ld x) { return Ld(__drcp_rn(x.v)); }
+__device__ __forceinline__ Ld ratio(Ld a, Ld b) { return Ld(__ddiv_rn(a.v, b.v)); }
+__device__ __forceinline__ unsigned gt_mask(Ld a, Ld b) { return a.v > b.v ? 1u : 0u; }
+__device__ __forceinline__ unsigned finite_mask(Ld a) { return isfinite(a.v) ? 1u : 0u; }
+__device__ __forceinline__ Ld select(unsigned m, Ld a, Ld b) { return (m & 1u) ? a : b; }
+
+// scalar arithmetic type -> one-node lane
+template <typename T> struct LaneOf;
+template <> struct LaneOf<float> { using type = Lf; };
+template <> struct LaneOf<double> { using type = Ld; };
+
+}  // namespace kbc

@@ -41,10 +41,18 @@ struct CodecScale {
 //   from_f64(d, i, c)   -> stored element from a double deviation
 // kVec: nodes per thread of the vector-row kernel (kVec * sizeof(S) bytes
 // per load/store; 16 for F64/F32, 8 for F16, which keeps F16 registers low).
+// kRowMinBlocks: resident 64-thread blocks per SM the vector-row kernel is
+// compiled for.  12 caps it at 80 registers (65536 / (12 * 64) = 85; KBC A/B
+// spill 20 bytes, which costs nothing measurable) and keeps 24 warps per SM
+// loading: 3% faster than 96 registers for KBC B and 5% for C/D.  Left free,
+// the compiler takes up to 190 registers and the bandwidth-bound FP32 step
+// loses a third of its rate.  FP64 is bound by its arithmetic pipe, not by
+// occupancy.
 struct CodecF64 {
     using S = double;
     using T = double;
     static constexpr int kVec = 2;
+    static constexpr int kRowMinBlocks = 1;
     __device__ __forceinline__ static T decode(S s, int, const CodecScale&) { return s; }
     __device__ __forceinline__ static S encode(T d, int, const CodecScale&) { return d; }
     __device__ __forceinline__ static double to_f64(S s, int, const CodecScale&) { return s; }
@@ -55,6 +63,7 @@ struct CodecF32 {
     using S = float;
     using T = float;
     static constexpr int kVec = 4;
+    static constexpr int kRowMinBlocks = 12;
     __device__ __forceinline__ static T decode(S s, int, const CodecScale&) { return s; }
     __device__ __forceinline__ static S encode(T d, int, const CodecScale&) { return d; }
     __device__ __forceinline__ static double to_f64(S s, int, const CodecScale&) { return (double)s; }
@@ -67,6 +76,7 @@ struct CodecF16 {
     using S = unsigned short;
     using T = float;
     static constexpr int kVec = 4;
+    static constexpr int kRowMinBlocks = 12;
     __device__ __forceinline__ static T decode(S s, int i, const CodecScale& c)
     {
         return __half2float(__ushort_as_half(s)) * ((float)wgt(i) * c.inv_scale);

@@ -259,15 +259,7 @@ step_tma(const typename C::S* __restrict__ src, typename C::S* __restrict__ dst,
         // this warp's operands are in registers: release the stage
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
-        unsigned hits = 0u;
-#pragma unroll
-        for (int q = 0; q < NV; ++q) {
-            T rho;
-            bool hit;
-            collide<VAR>(f[q], p, rho, hit);
-            bad |= !isfinite(rho);
-            hits |= (hit ? 1u : 0u) << q;
-        }
+        const unsigned hits = collide_vec<VAR>(f, p, bad);
         if constexpr (VAR != kLBGK) {
             if (a.fix_list) record_fix_mask<NV>(hits, y * a.nx + x0 + lx, a);
         }
