@@ -250,8 +250,16 @@ int kbc_diagnostics_noalloc(int nx, int ny, int variant, double beta, const doub
  * before returning: ceil(nsteps/ckpt_every) + ckpt_every + 1 population
  * fields, two adjoint fields and O(nx ny) doubles.  Synchronises the
  * stream.  Afterwards the handle holds g^nsteps.  The exact-gamma mode is
- * not differentiated (KBC_ERR_ARG).  Errors: KBC_ERR_ARG,
- * KBC_ERR_NOMEM, KBC_ERR_NONFINITE (the forward sweep blew up). */
+ * not differentiated (KBC_ERR_ARG).  With F32/F16 storage the nodes whose
+ * entropic denominator is at or below the guard (kbc_set_guard) are
+ * reversed in double, as the forward step evaluates them.
+ * Conditioning: the derivative of gamma* with respect to f carries
+ * |ds|/|dh| (Eq. result21 divides by <dh|dh>), so the exact discrete adjoint
+ * grows fast where <dh|dh> is tiny against <ds|ds> (smooth, well-resolved
+ * fields over many steps); single precision then overflows first.
+ * Errors: KBC_ERR_ARG, KBC_ERR_NOMEM, KBC_ERR_NONFINITE (the forward sweep
+ * blew up, or J, grad_beta or grad_u0 is not finite; the outputs are still
+ * written). */
 int kbc_adjoint(kbc_handle h, const double* rho0, const double* u0, int nsteps, int ckpt_every,
                 int objective, const double* u_target, double* J, double* grad_u0,
                 double* grad_beta);

@@ -19,15 +19,22 @@
 // function).
 #pragma once
 
+#include <type_traits>
+
 #include "kbc_kernels.cuh"
 
 namespace kbc {
 
+// Returns true when the entropic denominator rho <dh|dh> is at or below
+// p.guard (entropic gamma only): there the derivative of gamma* with respect
+// to f, which carries 1 / <dh|dh>, is not resolved in the lane's precision,
+// and the caller re-evaluates the node in double (as the forward step does).
 template <int VAR, typename T>
-__device__ __forceinline__ void collide_adjoint(const T (&d)[9], const T (&lam)[9],
+__device__ __forceinline__ bool collide_adjoint(const T (&d)[9], const T (&lam)[9],
                                                 const CollideParams<T>& p, T (&mu)[9],
                                                 T& beta_bar)
 {
+    bool guarded = false;
     constexpr bool central = (VAR == kA || VAR == kB);
     const T two_beta = p.two_beta;
     // ---------------------------------------------------------------- forward
@@ -89,6 +96,7 @@ __device__ __forceinline__ void collide_adjoint(const T (&d)[9], const T (&lam)[
         }
         T ch, R = T(0);
         const bool has_h = hh > T(0);
+        guarded = !p.fixed && p.guard > T(0) && !(hh > p.guard);
         const T ihh = has_h ? rcp_fast(hh) : T(0);
         if (p.fixed) {
             ch = p.ch_fixed;
@@ -180,6 +188,7 @@ __device__ __forceinline__ void collide_adjoint(const T (&d)[9], const T (&lam)[
 #pragma unroll
     for (int i = 0; i < 9; ++i) mu[i] += drhob + T(va(i)) * jxb + T(vb(i)) * jyb;
     beta_bar = bb;
+    return guarded;
 }
 
 // block-wide FP64 sum of v, added by thread 0 to *acc (fixed order)
@@ -195,12 +204,49 @@ __device__ __forceinline__ void block_add(double v, double* acc)
     if (threadIdx.x == 0) *acc += sm[0];
 }
 
+// Reverse step of node (x, y) entirely in double: pulls the forward state,
+// writes lambda^n to the nine sources and returns the node's beta adjoint.
+template <int VAR, class C>
+__device__ __forceinline__ double adj_node_f64(const typename C::S* __restrict__ g,
+                                               const typename C::T* __restrict__ lam_in,
+                                               typename C::T* __restrict__ lam_out, long long n,
+                                               int x, int y, const StepArgs& a)
+{
+    double dd[9], ll[9], mm[9], bnode;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const int ai = i % 3 - 1, bi = i / 3 - 1;
+        int sx = x - ai, sy = y - bi;
+        sx = sx < 0 ? sx + a.nx : (sx >= a.nx ? sx - a.nx : sx);
+        sy = sy < 0 ? sy + a.ny : (sy >= a.ny ? sy - a.ny : sy);
+        dd[i] = C::to_f64(g[(long long)i * a.plane + (long long)sy * a.nx + sx], i, a.cs);
+        ll[i] = (double)lam_in[(long long)i * a.plane + n];
+    }
+    CollideParams<double> q = a.pd;
+    q.guard = 0.0;
+    collide_adjoint<VAR>(dd, ll, q, mm, bnode);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const int ai = i % 3 - 1, bi = i / 3 - 1;
+        int sx = x - ai, sy = y - bi;
+        sx = sx < 0 ? sx + a.nx : (sx >= a.nx ? sx - a.nx : sx);
+        sy = sy < 0 ? sy + a.ny : (sy >= a.ny ? sy - a.ny : sy);
+        lam_out[(long long)i * a.plane + (long long)sy * a.nx + sx] = (typename C::T)mm[i];
+    }
+    return bnode;
+}
+
 // lambda^n from lambda^{n+1} and the forward state g^n; beta adjoint summed
 // into part[blockIdx.x] (same grid every step, so the sum order is fixed).
+// Single precision: a node whose entropic denominator is at or below the
+// guard (the nodes the forward step re-evaluates in double) is marked in
+// fixmask (bit n % 32 of word n / 32) and left to adj_fixup, which redoes it
+// in double.
 template <int VAR, class C>
 __global__ void __launch_bounds__(256)
 adj_step(const typename C::S* __restrict__ g, const typename C::T* __restrict__ lam_in,
-         typename C::T* __restrict__ lam_out, double* __restrict__ part, StepArgs a)
+         typename C::T* __restrict__ lam_out, double* __restrict__ part, unsigned* __restrict__ fixmask,
+         StepArgs a)
 {
     using T = typename C::T;
     const CollideParams<T>& p = params_of<T>(a);
@@ -221,7 +267,13 @@ adj_step(const typename C::S* __restrict__ g, const typename C::T* __restrict__ 
             lam[i] = lam_in[(long long)i * a.plane + n];
         }
         T bbar;
-        collide_adjoint<VAR>(d, lam, p, mu, bbar);
+        const bool guarded = collide_adjoint<VAR>(d, lam, p, mu, bbar);
+        if constexpr (!std::is_same<T, double>::value && VAR != kLBGK) {
+            if (guarded) {
+                atomicOr(fixmask + (n >> 5), 1u << (n & 31));
+                bbar = T(0);  // summed by adj_fixup
+            }
+        }
         bsum += (double)bbar;
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
@@ -230,6 +282,34 @@ adj_step(const typename C::S* __restrict__ g, const typename C::T* __restrict__ 
             sx = sx < 0 ? sx + a.nx : (sx >= a.nx ? sx - a.nx : sx);
             sy = sy < 0 ? sy + a.ny : (sy >= a.ny ? sy - a.ny : sy);
             lam_out[(long long)i * a.plane + (long long)sy * a.nx + sx] = mu[i];
+        }
+    }
+    block_add(bsum, part + blockIdx.x);
+}
+
+// Double-precision redo of the nodes adj_step marked: the mask is scanned in
+// a fixed order by the same grid, so the beta sum stays deterministic; each
+// word is cleared for the next step.
+template <int VAR, class C>
+__global__ void __launch_bounds__(256)
+adj_fixup(const typename C::S* __restrict__ g, const typename C::T* __restrict__ lam_in,
+          typename C::T* __restrict__ lam_out, double* __restrict__ part, unsigned* __restrict__ fixmask,
+          StepArgs a)
+{
+    const long long total = (long long)a.nx * a.ny;
+    const long long words = (total + 31) >> 5;
+    double bsum = 0.0;
+    for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < words;
+         w += (long long)gridDim.x * blockDim.x) {
+        unsigned m = fixmask[w];
+        if (m == 0u) continue;
+        fixmask[w] = 0u;
+        while (m) {
+            const int b = __ffs(m) - 1;
+            m &= m - 1u;
+            const long long n = (w << 5) + b;
+            const int y = (int)(n / a.nx), x = (int)(n - (long long)y * a.nx);
+            bsum += adj_node_f64<VAR, C>(g, lam_in, lam_out, n, x, y, a);
         }
     }
     block_add(bsum, part + blockIdx.x);
@@ -292,6 +372,7 @@ adj_grad_u0(const double* __restrict__ rho0, const double* __restrict__ ux0,
         }
         gx[n] = sx;
         gy[n] = sy;
+        if (!isfinite(sx) || !isfinite(sy)) atomicOr(a.flag, 8);  // adjoint overflowed
     }
 }
 

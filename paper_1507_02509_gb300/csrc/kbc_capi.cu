@@ -839,7 +839,10 @@ int kbc_adjoint(kbc_handle h, const double* rho0, const double* u0, int nsteps, 
     double* part = static_cast<double*>(B.get((size_t)(2 * nb + 8) * sizeof(double)));
     void* work[2] = {B.get(field), B.get(field)};
     void* lam[2] = {B.get(lamf), B.get(lamf)};
-    if (!in || !gdev || !part || !work[0] || !work[1] || !lam[0] || !lam[1])
+    // one bit per node: single-precision reverse steps left to the double redo
+    const size_t maskbytes = (size_t)((n + 31) / 32) * sizeof(unsigned);
+    unsigned* fixmask = static_cast<unsigned*>(B.get(maskbytes));
+    if (!in || !gdev || !part || !work[0] || !work[1] || !lam[0] || !lam[1] || !fixmask)
         return fail(h, KBC_ERR_NOMEM, "adjoint buffers");
     // checkpoints and segment states in two slabs
     char* ckslab = nseg ? static_cast<char*>(B.get(field * (size_t)nseg)) : nullptr;
@@ -852,6 +855,8 @@ int kbc_adjoint(kbc_handle h, const double* rho0, const double* u0, int nsteps, 
     if (e == cudaSuccess && objective == 1)
         e = cudaMemcpyAsync(in + 3 * n, u_target, 2 * n * sizeof(double), cudaMemcpyDefault, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(part, 0, (size_t)(2 * nb + 8) * sizeof(double), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(fixmask, 0, maskbytes, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->flag_dev, 0, sizeof(int), h->stream);  // fresh field
     if (e != cudaSuccess) return cuda_fail(h, e, "adjoint inputs");
     StepArgs a = args_of(h);
     e = by_codec(h->dtype, [&](auto c) {
@@ -904,7 +909,7 @@ int kbc_adjoint(kbc_handle h, const double* rho0, const double* u0, int nsteps, 
             e = by_codec(h->dtype, [&](auto c) {
                 using C = decltype(c);
                 return launch_adj_step<C>(h->variant, states[t - n0], lam[lc], lam[lc ^ 1],
-                                          part + nb, nb, a, h->stream);
+                                          part + nb, fixmask, nb, a, h->stream);
             });
             if (e != cudaSuccess) return cuda_fail(h, e, "adjoint step");
             lc ^= 1;
@@ -934,7 +939,12 @@ int kbc_adjoint(kbc_handle h, const double* rho0, const double* u0, int nsteps, 
     *J = host_sums[0];
     *grad_beta = host_sums[1];
     if (h->flag_host[0] & 2) return fail(h, KBC_ERR_TIMEOUT, "a device-side wait ran out");
-    if (h->flag_host[0]) return fail(h, KBC_ERR_NONFINITE, "non-finite populations in the forward sweep");
+    if (h->flag_host[0] & 1) return fail(h, KBC_ERR_NONFINITE, "non-finite populations in the forward sweep");
+    if ((h->flag_host[0] & 8) || !std::isfinite(*J) || !std::isfinite(*grad_beta))
+        return fail(h, KBC_ERR_NONFINITE,
+                    "the adjoint overflowed: the derivative of the entropic gamma* carries "
+                    "|ds|/|dh|, which is large where <dh|dh> is tiny against <ds|ds> "
+                    "(smooth fields); use FP64 storage or fewer steps");
     return KBC_OK;
 }
 

@@ -2,6 +2,8 @@
 // (kbc_f64.cu, kbc_f32.cu, kbc_f16.cu).
 #pragma once
 
+#include <type_traits>
+
 #include <cuda_runtime.h>
 
 #include "kbc_adjoint.cuh"
@@ -191,19 +193,27 @@ inline int adj_blocks(long long total, int num_sms) { return grid_for(total, 256
 
 template <class C>
 cudaError_t launch_adj_step(int variant, const void* g, const void* lam_in, void* lam_out,
-                            double* part, int nblocks, const StepArgs& a, cudaStream_t s)
+                            double* part, unsigned* fixmask, int nblocks, const StepArgs& a,
+                            cudaStream_t s)
 {
     using S = typename C::S;
     using T = typename C::T;
     const S* gp = static_cast<const S*>(g);
     const T* li = static_cast<const T*>(lam_in);
     T* lo = static_cast<T*>(lam_out);
+    constexpr bool fix = !std::is_same<T, double>::value;
     switch (variant) {
-    case kLBGK: adj_step<kLBGK, C><<<nblocks, 256, 0, s>>>(gp, li, lo, part, a); break;
-    case kA: adj_step<kA, C><<<nblocks, 256, 0, s>>>(gp, li, lo, part, a); break;
-    case kB: adj_step<kB, C><<<nblocks, 256, 0, s>>>(gp, li, lo, part, a); break;
-    case kC: adj_step<kC, C><<<nblocks, 256, 0, s>>>(gp, li, lo, part, a); break;
-    case kD: adj_step<kD, C><<<nblocks, 256, 0, s>>>(gp, li, lo, part, a); break;
+    case kLBGK: adj_step<kLBGK, C><<<nblocks, 256, 0, s>>>(gp, li, lo, part, fixmask, a); break;
+#define KBC_ADJ_CASE(V)                                                                  \
+    case V:                                                                              \
+        adj_step<V, C><<<nblocks, 256, 0, s>>>(gp, li, lo, part, fixmask, a);           \
+        if (fix) adj_fixup<V, C><<<nblocks, 256, 0, s>>>(gp, li, lo, part, fixmask, a); \
+        break;
+    KBC_ADJ_CASE(kA)
+    KBC_ADJ_CASE(kB)
+    KBC_ADJ_CASE(kC)
+    KBC_ADJ_CASE(kD)
+#undef KBC_ADJ_CASE
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -249,7 +259,7 @@ cudaError_t launch_adj_grad_u0(const double* rho0, const double* ux0, const doub
     extern template cudaError_t launch_diag_ext<C>(const void*, double*, int, double*,        \
                                                    const StepArgs&, cudaStream_t);            \
     extern template cudaError_t launch_adj_step<C>(int, const void*, const void*, void*,      \
-                                                   double*, int, const StepArgs&,             \
+                                                   double*, unsigned*, int, const StepArgs&,  \
                                                    cudaStream_t);                             \
     extern template cudaError_t launch_adj_objective<C>(const void*, const double*,           \
                                                         const double*, int, void*, double*,   \
@@ -276,7 +286,7 @@ cudaError_t launch_adj_grad_u0(const double* rho0, const double* ux0, const doub
     template cudaError_t launch_diag_ext<C>(const void*, double*, int, double*,               \
                                             const StepArgs&, cudaStream_t);                   \
     template cudaError_t launch_adj_step<C>(int, const void*, const void*, void*, double*,    \
-                                            int, const StepArgs&, cudaStream_t);              \
+                                            unsigned*, int, const StepArgs&, cudaStream_t);   \
     template cudaError_t launch_adj_objective<C>(const void*, const double*, const double*,   \
                                                  int, void*, double*, int, const StepArgs&,   \
                                                  cudaStream_t);                               \

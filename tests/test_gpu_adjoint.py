@@ -124,3 +124,21 @@ def test_fp32_adjoint_tracks_fp64_on_512():
     assert abs(J32 - J64) <= 1e-5 * J64
     assert rel_g < 1e-2
     assert abs(gb32 - gb64) <= 1e-2 * abs(gb64)
+
+
+def test_fp32_adjoint_overflow_is_reported():
+    """Smooth 512^2 field (k0 = 1), KBC B, 300 steps: the derivative of
+    gamma* carries |ds|/|dh| (Eq. result21 divides by <dh|dh>), which is large
+    on a smooth field, and the single-precision reverse sweep overflows.  The
+    call reports KBC_ERR_NONFINITE instead of returning non-finite gradients
+    as a success; the handle stays usable and the FP64 adjoint of the same
+    problem is finite."""
+    n, steps, K = 512, 300, 30
+    rho, ux, uy = flows.turbulence(n, k0=1, urms=0.03, seed=11)
+    beta = 1.0 / (6 * (n * 0.03 / 5000.0) + 1)
+    with pytest.raises(capi.KBCError) as ei:
+        _gpu_adjoint("B", "f32", beta, rho, ux, uy, steps, K, 0)
+    assert ei.value.status == capi.KBC_ERR_NONFINITE
+    assert "adjoint" in str(ei.value)
+    J, g, gb = _gpu_adjoint("B", "f64", beta, rho, ux, uy, steps, K, 0)
+    assert np.isfinite(J) and np.isfinite(gb) and np.all(np.isfinite(g))
