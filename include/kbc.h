@@ -253,10 +253,12 @@ int kbc_diagnostics_noalloc(int nx, int ny, int variant, double beta, const doub
  * not differentiated (KBC_ERR_ARG).  With F32/F16 storage the nodes whose
  * entropic denominator is at or below the guard (kbc_set_guard) are
  * reversed in double, as the forward step evaluates them.
- * Conditioning: the derivative of gamma* with respect to f carries
- * |ds|/|dh| (Eq. result21 divides by <dh|dh>), so the exact discrete adjoint
- * grows fast where <dh|dh> is tiny against <ds|ds> (smooth, well-resolved
- * fields over many steps); single precision then overflows first.
+ * Conditioning: where <dh|dh> is tiny (smooth, well-resolved fields)
+ * gamma* of Eq. result21 is poorly determined and leaves [0, 2/beta]; there
+ * the linearised relaxation of dh multiplies perturbations by |1 - beta
+ * gamma| > 1, so the discrete adjoint grows step by step (the forward state
+ * is unaffected because dh itself is tiny).  Over many steps the gradients
+ * become rounding-dominated; single precision overflows first.
  * Errors: KBC_ERR_ARG, KBC_ERR_NOMEM, KBC_ERR_NONFINITE (the forward sweep
  * blew up, or J, grad_beta or grad_u0 is not finite; the outputs are still
  * written). */

@@ -942,9 +942,9 @@ int kbc_adjoint(kbc_handle h, const double* rho0, const double* u0, int nsteps, 
     if (h->flag_host[0] & 1) return fail(h, KBC_ERR_NONFINITE, "non-finite populations in the forward sweep");
     if ((h->flag_host[0] & 8) || !std::isfinite(*J) || !std::isfinite(*grad_beta))
         return fail(h, KBC_ERR_NONFINITE,
-                    "the adjoint overflowed: the derivative of the entropic gamma* carries "
-                    "|ds|/|dh|, which is large where <dh|dh> is tiny against <ds|ds> "
-                    "(smooth fields); use FP64 storage or fewer steps");
+                    "the adjoint overflowed: where <dh|dh> is tiny gamma* leaves [0, 2/beta] "
+                    "and the linearised step amplifies by |1 - beta gamma| > 1 (smooth fields, "
+                    "many steps); use FP64 storage or fewer steps");
     return KBC_OK;
 }
 

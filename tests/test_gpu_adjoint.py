@@ -127,12 +127,12 @@ def test_fp32_adjoint_tracks_fp64_on_512():
 
 
 def test_fp32_adjoint_overflow_is_reported():
-    """Smooth 512^2 field (k0 = 1), KBC B, 300 steps: the derivative of
-    gamma* carries |ds|/|dh| (Eq. result21 divides by <dh|dh>), which is large
-    on a smooth field, and the single-precision reverse sweep overflows.  The
-    call reports KBC_ERR_NONFINITE instead of returning non-finite gradients
-    as a success; the handle stays usable and the FP64 adjoint of the same
-    problem is finite."""
+    """Smooth 512^2 field (k0 = 1), KBC B, 300 steps: where <dh|dh> is tiny
+    gamma* (Eq. result21) leaves [0, 2/beta], the linearised step amplifies
+    by |1 - beta gamma| > 1 and the single-precision reverse sweep
+    overflows.  The call reports KBC_ERR_NONFINITE instead of returning
+    non-finite gradients as a success; the handle stays usable and the FP64
+    adjoint of the same problem is finite."""
     n, steps, K = 512, 300, 30
     rho, ux, uy = flows.turbulence(n, k0=1, urms=0.03, seed=11)
     beta = 1.0 / (6 * (n * 0.03 / 5000.0) + 1)
