@@ -392,13 +392,22 @@ def run_ours(args):
             capi.kbc_adjoint(la.h, ra, ua, 20, 10, 0, None, g)  # warm-up
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            capi.kbc_adjoint(la.h, ra, ua, steps_a, ka, 0, None, g)
+            finite = True
+            try:
+                capi.kbc_adjoint(la.h, ra, ua, steps_a, ka, 0, None, g)
+            except capi.KBCError as e:
+                # past a few hundred steps of this field the linearised map
+                # amplifies (gamma* outside [0, 2/beta] where <dh|dh> is tiny)
+                if e.status != capi.KBC_ERR_NONFINITE:
+                    raise
+                finite = False
             ta = time.perf_counter() - t0
             extras[f"adjoint_{dt}"] = {
                 "seconds": round(ta, 3), "steps": steps_a, "ckpt_every": ka, "n": na,
                 "mlups_forward_equiv": round(na * na * steps_a / ta / 1e6, 1),
+                "gradients_finite": finite,
                 "what": "kbc_adjoint: forward with checkpoints + reverse sweep with segment "
-                        "recompute (3 stream-collide passes per step in all)"}
+                        "recompute (3 stream-collide passes per step in all); timing only"}
             la.close()
         del ra, xa, ya, ua
         torch.cuda.empty_cache()
