@@ -155,7 +155,10 @@ int kbc_guard_count(kbc_handle h, long long* count);
 int kbc_set_f16_scale(kbc_handle h, double scale);
 
 /* Initialise the field to the equilibrium f^eq(rho, u) of Eq. Eq at every
- * node.  rho: [ny][nx], u: [2][ny][nx]; host or device. */
+ * node.  rho: [ny][nx], u: [2][ny][nx]; host or device.  Host inputs of
+ * 64 MB and more are uploaded in row chunks on a second stream owned by the
+ * handle, each chunk's copy overlapping the initialisation of the previous
+ * one (same result as device inputs, bit for bit). */
 int kbc_init(kbc_handle h, const double* rho, const double* u);
 
 /* Initialise with Grad's approximation (Eq. Grad) using the pressure tensor
@@ -185,7 +188,10 @@ int kbc_sync(kbc_handle h, double timeout_s);
  * reported after the call synchronises). */
 int kbc_probe(kbc_handle h, int count, const long long* nodes, double* f);
 
-/* rho [ny][nx] and u [2][ny][nx] of the current field (FP64). */
+/* rho [ny][nx] and u [2][ny][nx] of the current field (FP64); host or
+ * device.  Host outputs of 64 MB and more are downloaded in row chunks on the
+ * handle's second stream, overlapping the computation of the next chunk;
+ * returns once the data are on the host. */
 int kbc_moments(kbc_handle h, double* rho, double* u);
 
 /* Global diagnostics (FP64 device reductions), out[KBC_DIAG_N] on the host:

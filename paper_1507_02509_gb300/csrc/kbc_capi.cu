@@ -116,6 +116,11 @@ std::string g_create_error;
 
 }  // namespace
 
+// Row chunks of the host <-> device pipelines of kbc_init and kbc_moments;
+// staging below kPipeMinBytes uses one copy and one kernel.
+constexpr int kPipeChunks = 8;
+constexpr size_t kPipeMinBytes = (size_t)64 << 20;
+
 struct kbc_ctx {
     int nx = 0, ny = 0, variant = 0, dtype = 0, device = 0, num_sms = 1;
     double beta = 1.0;
@@ -145,6 +150,10 @@ struct kbc_ctx {
     unsigned graph_version[4] = {0, 0, 0, 0};
     cudaGraphExec_t graph[4] = {nullptr, nullptr, nullptr, nullptr};
     cudaStream_t capture_stream = nullptr;
+    // host <-> device pipelines: copies of one row chunk overlap the kernel
+    // of the neighbouring chunk on this second stream, ordered by events
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t pipe_ev[kPipeChunks + 2] = {};
     cudaStream_t stream = nullptr;
     Allocator al;
     std::string err;
@@ -374,6 +383,82 @@ struct CallBuffers {
     }
 };
 
+// Device staging buffer of at least `bytes` (kept between calls).
+static int ensure_stage(kbc_ctx* h, size_t bytes)
+{
+    if (h->stage_bytes >= bytes) return KBC_OK;
+    dev_free(h, h->stage);
+    h->stage = dev_alloc(h, bytes);
+    h->stage_bytes = h->stage ? bytes : 0;
+    return h->stage ? KBC_OK : fail(h, KBC_ERR_NOMEM, "staging allocation failed");
+}
+
+// The copy stream and events of the pipelines (created on first use).
+static int pipe_ready(kbc_ctx* h)
+{
+    if (!h->copy_stream) {
+        cudaError_t e = cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            h->copy_stream = nullptr;
+            return cuda_fail(h, e, "copy stream");
+        }
+    }
+    for (cudaEvent_t& ev : h->pipe_ev) {
+        if (ev) continue;
+        cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            ev = nullptr;
+            return cuda_fail(h, e, "pipeline event");
+        }
+    }
+    return KBC_OK;
+}
+
+// Rows [y0, y0 + rows) of chunk k of the pipelines.
+static void pipe_chunk(const kbc_ctx* h, int k, int* y0, int* rows)
+{
+    const int per = (h->ny + kPipeChunks - 1) / kPipeChunks;
+    *y0 = k * per;
+    *rows = (*y0 >= h->ny) ? 0 : ((h->ny - *y0 < per) ? h->ny - *y0 : per);
+}
+
+// f = f^eq(rho, u) from host (or mixed) pointers: chunk k's uploads on the
+// copy stream overlap the init kernel of chunk k - 1 on the handle's stream
+// (init_feq works node by node, so a chunk is the same launch on fewer rows).
+static int init_feq_pipelined(kbc_ctx* h, const double* rho, const double* u)
+{
+    const size_t n = (size_t)h->nx * h->ny;
+    int rc = pipe_ready(h);
+    if (rc) return rc;
+    double* st = static_cast<double*>(h->stage);
+    // the staging buffer is free once earlier work on the handle's stream is done
+    cudaError_t e = cudaEventRecord(h->pipe_ev[kPipeChunks], h->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->copy_stream, h->pipe_ev[kPipeChunks], 0);
+    for (int k = 0; k < kPipeChunks && e == cudaSuccess; ++k) {
+        int y0, rows;
+        pipe_chunk(h, k, &y0, &rows);
+        if (rows == 0) break;
+        const size_t off = (size_t)y0 * h->nx, cnt = (size_t)rows * h->nx * sizeof(double);
+        e = cudaMemcpyAsync(st + off, rho + off, cnt, cudaMemcpyDefault, h->copy_stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(st + n + off, u + off, cnt, cudaMemcpyDefault, h->copy_stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(st + 2 * n + off, u + n + off, cnt, cudaMemcpyDefault, h->copy_stream);
+        if (e == cudaSuccess) e = cudaEventRecord(h->pipe_ev[k], h->copy_stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->pipe_ev[k], 0);
+        if (e != cudaSuccess) break;
+        StepArgs a = args_of(h);
+        a.ny = rows;
+        void* dst = static_cast<char*>(h->buf[h->cur]) + off * h->elem;
+        e = by_codec(h->dtype, [&](auto c) {
+            using C = decltype(c);
+            return launch_init<C>(st + off, st + n + off, st + 2 * n + off, dst, a, false,
+                                  h->stream, h->num_sms);
+        });
+    }
+    return e == cudaSuccess ? KBC_OK : cuda_fail(h, e, "pipelined field upload");
+}
+
 static int init_common(kbc_handle h, const double* rho, const double* u, bool grad)
 {
     int rc = check_h(h);
@@ -386,11 +471,13 @@ static int init_common(kbc_handle h, const double* rho, const double* u, bool gr
     const bool hr = !is_device_ptr(rho), hu = !is_device_ptr(u);
     if (hr || hu) {
         const size_t need = 3 * n * sizeof(double);
-        if (h->stage_bytes < need) {
-            dev_free(h, h->stage);
-            h->stage = dev_alloc(h, need);
-            h->stage_bytes = h->stage ? need : 0;
-            if (!h->stage) return fail(h, KBC_ERR_NOMEM, "staging allocation failed");
+        rc = ensure_stage(h, need);
+        if (rc) return rc;
+        if (!grad && need >= kPipeMinBytes) {
+            rc = init_feq_pipelined(h, rho, u);
+            if (rc) return rc;
+            h->initialized = true;
+            return KBC_OK;
         }
         double* st = static_cast<double*>(h->stage);
         cudaError_t e = cudaMemcpyAsync(st, rho, n * sizeof(double), cudaMemcpyDefault, h->stream);
@@ -533,6 +620,9 @@ int kbc_destroy(kbc_handle h)
     if (h->flag_host) cudaFreeHost(h->flag_host);
     drop_graphs(h);
     if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
+    if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
+    for (cudaEvent_t ev : h->pipe_ev)
+        if (ev) cudaEventDestroy(ev);
     cudaGetLastError();
     delete h;
     return KBC_OK;
@@ -775,13 +865,43 @@ int kbc_moments(kbc_handle h, double* rho, double* u)
     }
     // at least one host output: compute all three fields into staging
     const size_t bytes = 3 * n * sizeof(double);
-    if (h->stage_bytes < bytes) {
-        dev_free(h, h->stage);
-        h->stage = dev_alloc(h, bytes);
-        h->stage_bytes = h->stage ? bytes : 0;
-        if (!h->stage) return fail(h, KBC_ERR_NOMEM, "staging allocation failed");
-    }
+    rc = ensure_stage(h, bytes);
+    if (rc) return rc;
     double* st = static_cast<double*>(h->stage);
+    if (bytes >= kPipeMinBytes) {
+        // chunk k's downloads on the copy stream overlap the moments kernel of
+        // chunk k + 1 (the kernel works node by node)
+        rc = pipe_ready(h);
+        if (rc) return rc;
+        cudaError_t e = cudaSuccess;
+        for (int k = 0; k < kPipeChunks && e == cudaSuccess; ++k) {
+            int y0, rows;
+            pipe_chunk(h, k, &y0, &rows);
+            if (rows == 0) break;
+            const size_t off = (size_t)y0 * h->nx, cnt = (size_t)rows * h->nx * sizeof(double);
+            StepArgs ak = a;
+            ak.ny = rows;
+            const void* src = static_cast<const char*>(h->buf[h->cur]) + off * h->elem;
+            e = by_codec(h->dtype, [&](auto c) {
+                using C = decltype(c);
+                return launch_moments<C>(src, st + off, st + n + off, st + 2 * n + off, ak,
+                                         h->stream, h->num_sms);
+            });
+            if (e == cudaSuccess) e = cudaEventRecord(h->pipe_ev[k], h->stream);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(h->copy_stream, h->pipe_ev[k], 0);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(rho + off, st + off, cnt, cudaMemcpyDefault, h->copy_stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(u + off, st + n + off, cnt, cudaMemcpyDefault, h->copy_stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(u + n + off, st + 2 * n + off, cnt, cudaMemcpyDefault, h->copy_stream);
+        }
+        // the handle's stream resumes once the last download is done
+        if (e == cudaSuccess) e = cudaEventRecord(h->pipe_ev[kPipeChunks + 1], h->copy_stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->pipe_ev[kPipeChunks + 1], 0);
+        if (e != cudaSuccess) return cuda_fail(h, e, "pipelined moments");
+        return wait_stream(h, 0);
+    }
     cudaError_t e = by_codec(h->dtype, [&](auto c) {
         using C = decltype(c);
         return launch_moments<C>(h->buf[h->cur], st, st + n, st + 2 * n, a, h->stream, h->num_sms);
