@@ -48,6 +48,10 @@ def parse():
     p.add_argument("--e2e", type=int, default=1)
     p.add_argument("--cpu-baseline", type=int, default=1)
     p.add_argument("--seed", type=int, default=2024)
+    p.add_argument("--adjoint-steps", type=int, default=0,
+                   help="> 0: time only kbc_adjoint (KBC --variant, --dtype, n^2, this many "
+                        "steps, checkpoints every --ckpt) and print its JSON line")
+    p.add_argument("--ckpt", type=int, default=100)
     return p.parse_args()
 
 
@@ -474,10 +478,50 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_adjoint(args):
+    """kbc_adjoint alone: forward sweep with checkpoints, J, reverse sweep
+    with segment recompute; seeded turbulent field (k0 = n/64, u_rms = 0.03,
+    Re = 5000 on N), gradient of the final kinetic energy.  One warm-up call,
+    then min(--steps, 10) timed calls (wall clock around each synchronous
+    call; the median is reported)."""
+    import numpy as np
+    import torch
+
+    from paper_1507_02509_gb300 import Lattice, beta_from_viscosity, capi, flows
+
+    n = args.n
+    rho, ux, uy = flows.turbulence(n, k0=max(1.0, n / 64), urms=0.03, seed=args.seed,
+                                   backend="torch", device="cuda")
+    lat = Lattice(n, n, variant=args.variant, beta=beta_from_viscosity(n * 0.03 / 5000.0),
+                  dtype=args.dtype)
+    u = torch.stack((ux, uy)).contiguous()
+    g = torch.empty_like(u)
+    times, finite = [], True
+    for k in range(1 + max(1, min(args.steps, 10))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        try:
+            capi.kbc_adjoint(lat.h, rho, u, args.adjoint_steps, args.ckpt, 0, None, g)
+        except capi.KBCError as e:
+            if e.status != capi.KBC_ERR_NONFINITE:
+                raise
+            finite = False
+        if k:
+            times.append(time.perf_counter() - t0)
+    lat.close()
+    t = float(np.median(times))
+    print(json.dumps({"metric": "kbc_adjoint seconds", "value": round(t, 4), "unit": "s",
+                      "higher_is_better": False, "n": n, "variant": args.variant,
+                      "dtype": args.dtype, "steps": args.adjoint_steps, "ckpt_every": args.ckpt,
+                      "gradients_finite": finite, "data": "synthetic"}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.adjoint_steps > 0:
+        run_adjoint(args)
     else:
         run_ours(args)
 

@@ -202,12 +202,17 @@ cudaError_t launch_adj_step(int variant, const void* g, const void* lam_in, void
     const T* li = static_cast<const T*>(lam_in);
     T* lo = static_cast<T*>(lam_out);
     constexpr bool fix = !std::is_same<T, double>::value;
+    // the double redo scans one mask word per thread: a grid sized to the
+    // mask (at most the step's), so small grids do not pay for idle blocks;
+    // its beta partial sums land in part[0 .. fblocks) in a fixed order
+    const long long words = ((long long)a.nx * a.ny + 31) / 32;
+    const int fblocks = (int)((words + 255) / 256 < nblocks ? (words + 255) / 256 : nblocks);
     switch (variant) {
     case kLBGK: adj_step<kLBGK, C><<<nblocks, 256, 0, s>>>(gp, li, lo, part, fixmask, a); break;
 #define KBC_ADJ_CASE(V)                                                                  \
     case V:                                                                              \
         adj_step<V, C><<<nblocks, 256, 0, s>>>(gp, li, lo, part, fixmask, a);           \
-        if (fix) adj_fixup<V, C><<<nblocks, 256, 0, s>>>(gp, li, lo, part, fixmask, a); \
+        if (fix) adj_fixup<V, C><<<fblocks, 256, 0, s>>>(gp, li, lo, part, fixmask, a); \
         break;
     KBC_ADJ_CASE(kA)
     KBC_ADJ_CASE(kB)
