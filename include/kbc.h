@@ -117,10 +117,13 @@ int kbc_set_gamma_mode(kbc_handle h, int mode, double gamma_fixed);
 
 /* Kernel used by kbc_step (all of them share the collision arithmetic, so
  * they give identical bits):
- *   KBC_KERNEL_AUTO  (default) the vector-row kernel where nx is a multiple
- *                    of its row width, else the per-node kernel (the fastest
- *                    choice measured on GB300 at 4096^2 and 16384^2);
- *   KBC_KERNEL_ROWS  the same choice, named explicitly;
+ *   KBC_KERNEL_AUTO  (default) the fastest choice measured on GB300 at 4096^2
+ *                    and 16384^2: for F16 storage with a KBC variant the
+ *                    bulk-copy kernel below where nx is a multiple of 512,
+ *                    otherwise the vector-row kernel where nx is a multiple
+ *                    of its row width, else the per-node kernel;
+ *   KBC_KERNEL_ROWS  the vector-row kernel where nx allows it, else the
+ *                    per-node kernel;
  *   KBC_KERNEL_NODES the per-node kernel;
  *   KBC_KERNEL_BULK  the persistent, warp-specialised kernel that stages each
  *                    512-node row tile in shared memory with bulk
