@@ -25,11 +25,18 @@
  *           device buffer.  Caller memory is borrowed only for the duration
  *           of the call.
  * Ordering. All device work is issued on the stream bound with
- *           kbc_set_stream (default: the legacy default stream).  Calls
- *           that return device results into device memory are asynchronous
- *           on that stream; calls that return host results (host
- *           pointers, kbc_diagnostics, kbc_adjoint's scalars) synchronise
- *           that stream only, with a bounded wait (KBC_ERR_TIMEOUT).
+ *           kbc_set_stream (default: the legacy default stream), except the
+ *           chunked host transfers of kbc_init / kbc_moments, which use a
+ *           second stream owned by the handle and are ordered against the
+ *           bound stream with events (the bound stream sees them as part of
+ *           the call).  Calls that return device results into device memory
+ *           are asynchronous on that stream; calls that return host results
+ *           (host pointers, kbc_diagnostics, kbc_adjoint's scalars)
+ *           synchronise that stream only, with a bounded wait
+ *           (KBC_ERR_TIMEOUT).
+ * Threads.  A handle is not thread-safe: calls on one handle must not run
+ *           concurrently.  Different handles may be used from different
+ *           host threads.
  * State.    After kbc_init and n steps the handle holds the post-collision
  *           field f'(., n) of Eq. Egeneral.  rho and u are the same for the
  *           pre- and post-collision fields because the collision conserves
