@@ -261,7 +261,28 @@ __device__ __forceinline__ L collide(L (&d)[9], const CollideParams<typename L::
         L x[9], w[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) x[i] = fmaL(L(wgt(i)), P[i], L(wgt(i)));  // f^eq_i / rho
-        inv9(x, w);  // w_i = rho / f^eq_i
+        constexpr bool dbl = std::is_same<typename L::S, double>::value;
+        L xprod;  // double lanes: prod_i x_i, the common factor of their weights
+        if constexpr (dbl) {
+            // gamma* uses the weights only through <ds|dh> / <dh|dh>, which a
+            // common factor leaves unchanged: w_i = prod_{j != i} x_j from
+            // prefix and suffix products, with no division (the FP64 pipe is
+            // the bound of the double path)
+            L pre[8], suf[9];
+            pre[0] = x[0];
+#pragma unroll
+            for (int k = 1; k < 8; ++k) pre[k] = pre[k - 1] * x[k];
+            suf[8] = x[8];
+#pragma unroll
+            for (int k = 7; k >= 1; --k) suf[k] = suf[k + 1] * x[k];
+            w[0] = suf[1];
+            w[8] = pre[7];
+#pragma unroll
+            for (int k = 1; k < 8; ++k) w[k] = pre[k - 1] * suf[k + 1];
+            xprod = pre[7] * x[8];
+        } else {
+            inv9(x, w);  // w_i = rho / f^eq_i
+        }
         L dh[9];
         L sh, hh;
 #pragma unroll
@@ -282,9 +303,13 @@ __device__ __forceinline__ L collide(L (&d)[9], const CollideParams<typename L::
             nch = L(-p.ch_fixed);
             gamma = L(p.gamma_fixed);
         } else {
-            if (p.guard > 0) guard_hits = ~gt_mask(hh, L(p.guard)) & ((1u << L::kLanes) - 1u);
+            // the guard concerns single precision (double lanes never flag)
+            if (!dbl && p.guard > 0) guard_hits = ~gt_mask(hh, L(p.guard)) & ((1u << L::kLanes) - 1u);
             // <dh|dh> = 0 means dh = 0: gamma multiplies nothing; report 2
-            const unsigned pos = gt_mask(hh, L(0));
+            // (double lanes: the sign of <dh|dh> is that of hh * prod x)
+            unsigned pos;
+            if constexpr (dbl) pos = gt_mask(hh * xprod, L(0));
+            else pos = gt_mask(hh, L(0));
             const L R = ratio(sh, hh);
             const L nb = L(-p.one_m_2beta);
             nch = select(pos, fmaL(nb, R, nb), L(0));
@@ -292,11 +317,12 @@ __device__ __forceinline__ L collide(L (&d)[9], const CollideParams<typename L::
             if constexpr (std::is_same<L, Ld>::value) {
                 if (p.exact && pos) {
                     double dsd[9], dhd[9], wd[9];
+                    const double iprod = 1.0 / xprod.v;  // weights normalised: rho / f^eq_i
 #pragma unroll
                     for (int i = 0; i < 9; ++i) {
                         dsd[i] = ds[i].v;
                         dhd[i] = dh[i].v;
-                        wd[i] = w[i].v;
+                        wd[i] = w[i].v * iprod;
                     }
                     const double beta = 0.5 * p.two_beta;
                     gamma = Ld(exact_gamma(dsd, dhd, wd, rho.v, beta, gamma.v));
