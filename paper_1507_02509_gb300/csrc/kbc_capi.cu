@@ -368,6 +368,50 @@ static cudaGraphExec_t step_graph(kbc_handle h)
     return exec;
 }
 
+// Instantiated graph of the work `issue(stream)` enqueues on the private
+// capture stream (returns false on a failed launch); nullptr when capture or
+// instantiation fails, with the handle's guard parity restored, so that the
+// caller can fall back to launching the same work directly.
+template <class F>
+static cudaGraphExec_t capture_work(kbc_handle h, F&& issue)
+{
+    if (!h->capture_stream &&
+        cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        h->capture_stream = nullptr;
+        return nullptr;
+    }
+    const int slot0 = h->fix_slot;
+    if (cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    const bool ok = issue(h->capture_stream);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(h->capture_stream, &g);
+    cudaGraphExec_t exec = nullptr;
+    if (!(ok && e == cudaSuccess && g && cudaGraphInstantiate(&exec, g, 0) == cudaSuccess)) {
+        exec = nullptr;
+        h->fix_slot = slot0;
+    }
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return exec;
+}
+
+// Graphs of one kbc_adjoint call (its buffers are the call's own).
+struct AdjointGraphs {
+    cudaGraphExec_t fwd = nullptr;              // ckpt_every forward steps from work[0]
+    cudaGraphExec_t rec[2] = {nullptr, nullptr}; // segment recompute, by starting guard parity
+    int rec_flip[2] = {0, 0};                    // guard parity change of one recompute
+    cudaGraphExec_t rev[2] = {nullptr, nullptr}; // reverse segment, by lambda parity
+    ~AdjointGraphs()
+    {
+        for (cudaGraphExec_t g : {fwd, rec[0], rec[1], rev[0], rev[1]})
+            if (g) cudaGraphExecDestroy(g);
+    }
+};
+
 // device buffers owned by one call, released on every exit path
 struct CallBuffers {
     kbc_ctx* h;
@@ -974,6 +1018,13 @@ int kbc_adjoint(kbc_handle h, const double* rho0, const double* u0, int nsteps, 
     char* segslab = seglen > 1 ? static_cast<char*>(B.get(field * (size_t)(seglen - 1))) : nullptr;
     if ((nseg && !ckslab) || (seglen > 1 && !segslab))
         return fail(h, KBC_ERR_NOMEM, "adjoint checkpoint storage");
+    // Full segments (ckpt_every steps, even) replay captured graphs: the
+    // sweep is otherwise launch-bound on small grids.  The recompute starts
+    // from a fixed copy of the segment's checkpoint so that its graph's
+    // pointers do not change from segment to segment.
+    AdjointGraphs G;
+    void* ckwork = (K % 2 == 0 && h->graph_steps > 0 && nsteps >= K) ? B.get(field) : nullptr;
+    const bool graphs = ckwork != nullptr;
     cudaError_t e = cudaMemcpyAsync(in, rho0, n * sizeof(double), cudaMemcpyDefault, h->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(in + n, u0, 2 * n * sizeof(double), cudaMemcpyDefault, h->stream);
@@ -991,15 +1042,33 @@ int kbc_adjoint(kbc_handle h, const double* rho0, const double* u0, int nsteps, 
     if (e != cudaSuccess) return cuda_fail(h, e, "adjoint init");
     // forward sweep, keeping g^{sK}
     int cur = 0;
-    for (int t = 0; t < nsteps; ++t) {
+    for (int t = 0; t < nsteps;) {
         if (t % K == 0) {
             e = cudaMemcpyAsync(ckslab + field * (size_t)(t / K), work[cur], field,
                                 cudaMemcpyDeviceToDevice, h->stream);
             if (e != cudaSuccess) return cuda_fail(h, e, "checkpoint copy");
+            if (graphs && cur == 0 && t + K <= nsteps) {
+                // K (even) steps return to work[0] and to the same guard parity
+                if (!G.fwd) {
+                    G.fwd = capture_work(h, [&](cudaStream_t cs) {
+                        int c = 0;
+                        for (int j = 0; j < K; ++j, c ^= 1)
+                            if (step_into(h, work[c], work[c ^ 1], cs, true) != KBC_OK) return false;
+                        return true;
+                    });
+                }
+                if (G.fwd) {
+                    e = cudaGraphLaunch(G.fwd, h->stream);
+                    if (e != cudaSuccess) return cuda_fail(h, e, "adjoint forward graph");
+                    t += K;
+                    continue;
+                }
+            }
         }
         rc = step_into(h, work[cur], work[cur ^ 1]);
         if (rc) return rc;
         cur ^= 1;
+        ++t;
     }
     const void* gN = work[cur];
     // J and lambda^N
@@ -1022,12 +1091,64 @@ int kbc_adjoint(kbc_handle h, const double* rho0, const double* u0, int nsteps, 
         const int n1 = (n0 + K < nsteps) ? n0 + K : nsteps;
         const int len = n1 - n0;
         std::vector<const void*> states((size_t)len);
+        const bool full = graphs && len == K;
         states[0] = ckslab + field * (size_t)sgi;
-        for (int j = 1; j < len; ++j) {
-            void* dst = segslab + field * (size_t)(j - 1);
-            rc = step_into(h, states[j - 1], dst);
+        if (full) {
+            e = cudaMemcpyAsync(ckwork, states[0], field, cudaMemcpyDeviceToDevice, h->stream);
+            if (e != cudaSuccess) return cuda_fail(h, e, "checkpoint copy");
+            states[0] = ckwork;
+        }
+        for (int j = 1; j < len; ++j) states[j] = segslab + field * (size_t)(j - 1);
+        bool done = false;
+        if (full) {
+            const int slot = h->fix_slot & 1;
+            if (G.rec[slot]) {
+                e = cudaGraphLaunch(G.rec[slot], h->stream);
+                if (e != cudaSuccess) return cuda_fail(h, e, "adjoint recompute graph");
+                h->fix_slot ^= G.rec_flip[slot];
+                done = true;
+            } else {
+                G.rec[slot] = capture_work(h, [&](cudaStream_t cs) {
+                    for (int j = 1; j < len; ++j)
+                        if (step_into(h, states[j - 1], const_cast<void*>(states[j]), cs, true) != KBC_OK)
+                            return false;
+                    return true;
+                });
+                if (G.rec[slot]) {
+                    // capture advanced the parity as the replay will
+                    G.rec_flip[slot] = (h->fix_slot ^ slot) & 1;
+                    e = cudaGraphLaunch(G.rec[slot], h->stream);
+                    if (e != cudaSuccess) return cuda_fail(h, e, "adjoint recompute graph");
+                    done = true;
+                }
+            }
+        }
+        for (int j = 1; j < len && !done; ++j) {
+            rc = step_into(h, states[j - 1], const_cast<void*>(states[j]));
             if (rc) return rc;
-            states[j] = dst;
+        }
+        if (full) {
+            if (!G.rev[lc]) {
+                const int l0 = lc;
+                G.rev[lc] = capture_work(h, [&](cudaStream_t cs) {
+                    int l = l0;
+                    StepArgs ar = args_of(h);
+                    for (int t = n1 - 1; t >= n0; --t, l ^= 1) {
+                        cudaError_t ec = by_codec(h->dtype, [&](auto c) {
+                            using C = decltype(c);
+                            return launch_adj_step<C>(h->variant, states[t - n0], lam[l], lam[l ^ 1],
+                                                      part + nb, fixmask, nb, ar, cs);
+                        });
+                        if (ec != cudaSuccess) return false;
+                    }
+                    return true;
+                });
+            }
+            if (G.rev[lc]) {
+                e = cudaGraphLaunch(G.rev[lc], h->stream);
+                if (e != cudaSuccess) return cuda_fail(h, e, "adjoint reverse graph");
+                continue;  // K (even) reverse steps leave lc unchanged
+            }
         }
         for (int t = n1 - 1; t >= n0; --t) {
             a = args_of(h);

@@ -87,7 +87,8 @@ __device__ __forceinline__ void record_fix(bool hit, int n, const StepArgs& a)
     int base = 0;
     if (lane == leader) base = atomicAdd(a.fix_count + a.fix_slot, __popc(m));
     base = __shfl_sync(active, base, leader);
-    if (hit) a.fix_list[base + __popc(m & ((1u << lane) - 1u))] = n;
+    const int idx = base + __popc(m & ((1u << lane) - 1u));
+    if (hit && idx < a.nx * a.ny) a.fix_list[idx] = n;  // the list holds one entry per node
 }
 
 template <typename T> __device__ __forceinline__ const CollideParams<T>& params_of(const StepArgs& a);
@@ -108,9 +109,13 @@ __device__ __forceinline__ void record_fix_mask(unsigned hits, int n0, const Ste
     if (!__any_sync(0xffffffffu, hits != 0u)) return;
     if (hits) {
         int base = atomicAdd(a.fix_count + a.fix_slot, __popc(hits));
+        const int cap = a.nx * a.ny;  // the list holds one entry per node
 #pragma unroll
         for (int k = 0; k < NV; ++k)
-            if (hits & (1u << k)) a.fix_list[base++] = n0 + k;
+            if (hits & (1u << k)) {
+                if (base < cap) a.fix_list[base] = n0 + k;
+                ++base;
+            }
     }
 }
 
@@ -300,7 +305,8 @@ __global__ void __launch_bounds__(256)
 step_fixup(const typename C::S* __restrict__ src, typename C::S* __restrict__ dst, StepArgs a)
 {
     using S = typename C::S;
-    const int count = a.fix_count[a.fix_slot];
+    const int recorded = a.fix_count[a.fix_slot];
+    const int count = recorded < a.nx * a.ny ? recorded : a.nx * a.ny;
     if (count == 0) return;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < count; t += gridDim.x * blockDim.x) {
         const int n = a.fix_list[t];

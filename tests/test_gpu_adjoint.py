@@ -26,9 +26,12 @@ def _case(n, seed, k0=2.0, urms=0.05):
     return rho, ux, uy, tx, ty
 
 
-def _gpu_adjoint(variant, dtype, beta, rho, ux, uy, steps, K, objective, tx=None, ty=None):
+def _gpu_adjoint(variant, dtype, beta, rho, ux, uy, steps, K, objective, tx=None, ty=None,
+                 guard=None):
     ny, nx = rho.shape
     lat = Lattice(nx, ny, variant=variant, beta=beta, dtype=dtype)
+    if guard is not None:
+        lat.set_guard(guard)
     u = np.ascontiguousarray(np.stack((ux, uy)))
     tgt = np.ascontiguousarray(np.stack((tx, ty))) if objective == 1 else None
     g = np.empty((2, ny, nx))
@@ -81,13 +84,19 @@ def test_adjoint_matches_finite_differences(variant):
     assert gb == pytest.approx(fd, rel=1e-6)
 
 
-@pytest.mark.parametrize("dtype", ["f64", "f32"])
-def test_checkpoint_interval_does_not_change_gradients(dtype):
+@pytest.mark.parametrize("dtype,guard", [("f64", None), ("f32", None), ("f32", 1e-10)])
+def test_checkpoint_interval_does_not_change_gradients(dtype, guard):
     """Recomputed segments are bit-identical to the forward sweep, so the
-    gradients do not depend on the checkpoint interval."""
+    gradients do not depend on the checkpoint interval.  Even intervals that
+    fit the run (6, 10, 30) replay captured graphs of whole segments, several
+    of them for 6 and 10, whose recompute changes the FP32 guard's counter
+    parity from one segment to the next; odd ones (1, 7) and 100 launch step
+    by step.  The guard at 1e-10 sends many nodes through the FP64
+    re-evaluation every step, so that its counters carry real counts."""
     n, steps = 128, 30
     rho, ux, uy, tx, ty = _case(n, 3, k0=4.0)
-    out = [_gpu_adjoint("B", dtype, 0.98, rho, ux, uy, steps, K, 0) for K in (1, 7, 30, 100)]
+    out = [_gpu_adjoint("B", dtype, 0.98, rho, ux, uy, steps, K, 0, guard=guard)
+           for K in (1, 6, 7, 10, 30, 100)]
     for J, g, gb in out[1:]:
         assert J == out[0][0] and gb == out[0][2]
         assert np.array_equal(g, out[0][1])
