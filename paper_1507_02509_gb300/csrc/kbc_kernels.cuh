@@ -308,7 +308,9 @@ step_fixup(const typename C::S* __restrict__ src, typename C::S* __restrict__ ds
     const int recorded = a.fix_count[a.fix_slot];
     const int count = recorded < a.nx * a.ny ? recorded : a.nx * a.ny;
     if (count == 0) return;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < count; t += gridDim.x * blockDim.x) {
+    // node t goes to block t % gridDim.x: the few recorded nodes spread over
+    // every SM's FP64 pipe instead of filling the first blocks
+    for (int t = threadIdx.x * gridDim.x + blockIdx.x; t < count; t += gridDim.x * blockDim.x) {
         const int n = a.fix_list[t];
         const int y = n / a.nx, x = n - y * a.nx;
         double f[9];
