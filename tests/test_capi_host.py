@@ -5,6 +5,8 @@ device work."""
 import ctypes
 import os
 import re
+import shutil
+import subprocess
 
 import pytest
 
@@ -94,3 +96,41 @@ def test_table3_definitions():
     for re_, n, e0, z0, nu, te in rows:
         assert viscosity_for_reynolds(int(n), e0, re_) == pytest.approx(nu, rel=2e-3)
         assert z0 ** -0.5 == pytest.approx(te, rel=3e-3)
+
+
+C_CALLER = r"""
+#include <stdio.h>
+#include <string.h>
+#include "kbc.h"
+
+int main(void)
+{
+    kbc_handle h = 0;
+    double bytes = 0.0;
+    /* an empty grid is rejected before any device work */
+    if (kbc_create(0, 8, KBC_B, 0.9, KBC_F32_DEV, &h) != KBC_ERR_ARG || h != 0) return 1;
+    if (strlen(kbc_last_error(0)) == 0) return 2;
+    if (kbc_bytes_per_update(0, &bytes) != KBC_ERR_ARG) return 3;
+    printf("%s\n", kbc_last_error(0));
+    return 0;
+}
+"""
+
+
+def test_header_compiles_as_c_and_links(lib, tmp_path):
+    """A plain C99 caller (no C++) compiles against include/kbc.h with all
+    warnings as errors, links against the in-tree library and gets the
+    documented status codes."""
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "caller.c"
+    src.write_text(C_CALLER)
+    exe = tmp_path / "caller"
+    libdir = os.path.dirname(kbuild.LIB)
+    subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    str(src), "-L", libdir, "-lkbc_gb300", f"-Wl,-rpath,{libdir}", "-o", str(exe)],
+                   check=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, (r.returncode, r.stdout, r.stderr)
+    assert "grid" in r.stdout
