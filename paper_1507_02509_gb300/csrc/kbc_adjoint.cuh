@@ -25,6 +25,19 @@
 
 namespace kbc {
 
+// Threads per block of the reverse step, and resident blocks per SM it is
+// compiled for: the natural-basis variants (C, D) fit 96 registers (5 blocks,
+// 20 warps per SM) without spilling; the central-basis ones keep 128 (4
+// blocks), where a 96-register cap spills and runs slower.  Measured at
+// 4096^2 (200 steps, FP32): B 0.203 s with 256-thread blocks -> 0.199 s,
+// C 0.197 s -> 0.185 s with the 96-register cap; 512^2: B 0.063 -> 0.055 s.
+// Double arithmetic is bound by the FP64 pipe, not by occupancy: no cap.
+constexpr int kAdjBlock = 128;
+template <int VAR, typename T> constexpr int adj_min_blocks()
+{
+    return std::is_same<T, double>::value ? 1 : ((VAR == kC || VAR == kD) ? 5 : 4);
+}
+
 // Returns true when the entropic denominator rho <dh|dh> is at or below
 // p.guard (entropic gamma only): there the derivative of gamma* with respect
 // to f, which carries 1 / <dh|dh>, is not resolved in the lane's precision,
@@ -262,7 +275,7 @@ __device__ __forceinline__ double adj_node_f64(const typename C::S* __restrict__
 // fixmask (bit n % 32 of word n / 32) and left to adj_fixup, which redoes it
 // in double.
 template <int VAR, class C>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kAdjBlock, adj_min_blocks<VAR, typename C::T>())
 adj_step(const typename C::S* __restrict__ g, const typename C::T* __restrict__ lam_in,
          typename C::T* __restrict__ lam_out, double* __restrict__ part, unsigned* __restrict__ fixmask,
          StepArgs a)

@@ -208,10 +208,10 @@ cudaError_t launch_adj_step(int variant, const void* g, const void* lam_in, void
     const long long words = ((long long)a.nx * a.ny + 31) / 32;
     const int fblocks = (int)((words + 255) / 256 < nblocks ? (words + 255) / 256 : nblocks);
     switch (variant) {
-    case kLBGK: adj_step<kLBGK, C><<<nblocks, 256, 0, s>>>(gp, li, lo, part, fixmask, a); break;
+    case kLBGK: adj_step<kLBGK, C><<<nblocks, kAdjBlock, 0, s>>>(gp, li, lo, part, fixmask, a); break;
 #define KBC_ADJ_CASE(V)                                                                  \
     case V:                                                                              \
-        adj_step<V, C><<<nblocks, 256, 0, s>>>(gp, li, lo, part, fixmask, a);           \
+        adj_step<V, C><<<nblocks, kAdjBlock, 0, s>>>(gp, li, lo, part, fixmask, a);     \
         if (fix) adj_fixup<V, C><<<fblocks, 256, 0, s>>>(gp, li, lo, part, fixmask, a); \
         break;
     KBC_ADJ_CASE(kA)
