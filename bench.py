@@ -318,6 +318,12 @@ def run_ours(args):
         h_u[1].copy_(uy)
         o_rho = torch.empty((n, n), dtype=torch.float64, pin_memory=True)
         o_u = torch.empty((2, n, n), dtype=torch.float64, pin_memory=True)
+        # untimed warm-up of the same sequence: the library's first host
+        # transfer allocates its staging buffer and copy stream
+        capi.kbc_init(lat.h, h_rho, h_u)
+        capi.kbc_step(lat.h, 1)
+        capi.kbc_moments(lat.h, o_rho, o_u)
+        lat.sync()
         torch.cuda.synchronize()
         barrier()
         t0 = time.perf_counter()
