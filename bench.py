@@ -52,6 +52,8 @@ def parse():
                    help="> 0: time only kbc_adjoint (KBC --variant, --dtype, n^2, this many "
                         "steps, checkpoints every --ckpt) and print its JSON line")
     p.add_argument("--ckpt", type=int, default=100)
+    p.add_argument("--diag-only", type=int, default=0,
+                   help="1: time only kbc_diagnostics and kbc_diagnostics_ext on n^2")
     return p.parse_args()
 
 
@@ -522,12 +524,48 @@ def run_adjoint(args):
                       "gradients_finite": finite, "data": "synthetic"}))
 
 
+def run_diagnostics(args):
+    """kbc_diagnostics and kbc_diagnostics_ext alone on the seeded turbulent
+    field (--variant, --dtype, n^2): one warm-up call each, then the median of
+    min(--steps, 10) timed calls (each returns its values on the host)."""
+    import numpy as np
+    import torch
+
+    from paper_1507_02509_gb300 import Lattice, beta_from_viscosity, capi, flows
+
+    n = args.n
+    rho, ux, uy = flows.turbulence(n, k0=16, urms=0.03, seed=args.seed, backend="torch",
+                                   device="cuda")
+    lat = Lattice(n, n, variant=args.variant, beta=beta_from_viscosity(n * 0.03 / 1e5),
+                  dtype=args.dtype)
+    lat.init(rho, ux, uy)
+    lat.sync()
+    res = {}
+    for name, fn, k in (("diagnostics", capi.kbc_diagnostics, capi.KBC_DIAG_N),
+                        ("diagnostics_ext", capi.kbc_diagnostics_ext, capi.KBC_DIAG_EXT_N)):
+        out = np.zeros(k)
+        times = []
+        for r in range(1 + max(1, min(args.steps, 10))):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            fn(lat.h, out)
+            if r:
+                times.append(time.perf_counter() - t0)
+        res[name] = round(float(np.median(times)) * 1e3, 3)
+    lat.close()
+    print(json.dumps({"metric": "diagnostics ms per call", "value": res["diagnostics"], "unit": "ms",
+                      "higher_is_better": False, "diagnostics_ext_ms": res["diagnostics_ext"],
+                      "n": n, "variant": args.variant, "dtype": args.dtype, "data": "synthetic"}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.adjoint_steps > 0:
         run_adjoint(args)
+    elif args.diag_only:
+        run_diagnostics(args)
     else:
         run_ours(args)
 

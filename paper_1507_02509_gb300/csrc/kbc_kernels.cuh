@@ -477,54 +477,70 @@ __global__ void moments(const typename C::S* __restrict__ src, double* __restric
 constexpr int kDiagParts = 10;
 constexpr int kDiagBlock = 256;
 
+// Tiles of the diagnostics kernels: kTileW x kTileH nodes per block
+// iteration (two per thread), with rho and u computed once per position of
+// the tile and its halo into shared memory (periodic wrap), so that the
+// central-difference stencils read them there instead of recomputing them.
+constexpr int kTileW = 64, kTileH = 8;
+
+__device__ __forceinline__ int wrap_mod(int v, int n)
+{
+    v %= n;
+    return v < 0 ? v + n : v;
+}
+
 template <int VAR, class C>
 __global__ void __launch_bounds__(kDiagBlock)
 diag_partial(const typename C::S* __restrict__ src, double* __restrict__ part, StepArgs a)
 {
-    const long long total = (long long)a.nx * a.ny;
+    constexpr int HW = kTileW + 2, HH = kTileH + 2;  // one-node halo
+    __shared__ double sr[HH][HW], sux[HH][HW], suy[HH][HW];
     double acc[kDiagParts] = {0, 0, 0, 0, 0, 0, 0, 0, 1e300, -1e300};
     CollideParams<double> p = a.pd;
     p.guard = 0.0;
-    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < total;
-         n += (long long)gridDim.x * blockDim.x) {
-        const int y = (int)(n / a.nx), x = (int)(n - (long long)y * a.nx);
-        double r, ux, uy;
-        node_macro<C>(src, n, a, r, ux, uy);
-        acc[0] += r;
-        acc[1] += r * ux;
-        acc[2] += r * uy;
-        const double ke = 0.5 * (ux * ux + uy * uy);
-        acc[3] += ke;
-        acc[4] += ke * ke;
-        const long long row = (long long)y * a.nx;
-        const long long xp = row + (x + 1 == a.nx ? 0 : x + 1);
-        const long long xm = row + (x == 0 ? a.nx - 1 : x - 1);
-        const long long yp = (long long)(y + 1 == a.ny ? 0 : y + 1) * a.nx + x;
-        const long long ym = (long long)(y == 0 ? a.ny - 1 : y - 1) * a.nx + x;
-        double r1, uxp, uyp, uxm, uym, uxyp, uyyp, uxym, uyym;
-        node_macro<C>(src, xp, a, r1, uxp, uyp);
-        node_macro<C>(src, xm, a, r1, uxm, uym);
-        node_macro<C>(src, yp, a, r1, uxyp, uyyp);
-        node_macro<C>(src, ym, a, r1, uxym, uyym);
-        const double w = 0.5 * (uyp - uym) - 0.5 * (uxyp - uxym);
-        const double zz = 0.5 * w * w;
-        acc[5] += zz;
-        acc[6] += zz * zz;
-        double f[9];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            const int ai = i % 3 - 1, bi = i / 3 - 1;
-            int sx = x - ai, sy = y - bi;
-            sx = sx < 0 ? sx + a.nx : (sx >= a.nx ? sx - a.nx : sx);
-            sy = sy < 0 ? sy + a.ny : (sy >= a.ny ? sy - a.ny : sy);
-            f[i] = C::to_f64(src[(long long)i * a.plane + (long long)sy * a.nx + sx], i, a.cs);
+    const int ntx = (a.nx + kTileW - 1) / kTileW, nty = (a.ny + kTileH - 1) / kTileH;
+    const long long ntiles = (long long)ntx * nty;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int x0 = (int)(tile % ntx) * kTileW, y0 = (int)(tile / ntx) * kTileH;
+        __syncthreads();  // the previous tile's readers are done with the arrays
+        for (int q = threadIdx.x; q < HH * HW; q += blockDim.x) {
+            const int qy = q / HW, qx = q - qy * HW;
+            const int gx = wrap_mod(x0 + qx - 1, a.nx), gy = wrap_mod(y0 + qy - 1, a.ny);
+            node_macro<C>(src, (long long)gy * a.nx + gx, a, sr[qy][qx], sux[qy][qx], suy[qy][qx]);
         }
-        double rr;
-        bool hit;
-        const double g = collide_node<VAR>(f, p, rr, hit);
-        acc[7] += g;
-        acc[8] = fmin(acc[8], g);
-        acc[9] = fmax(acc[9], g);
+        __syncthreads();
+        for (int k = threadIdx.x; k < kTileW * kTileH; k += blockDim.x) {
+            const int ly = k / kTileW, lx = k - ly * kTileW;
+            const int x = x0 + lx, y = y0 + ly;
+            if (x >= a.nx || y >= a.ny) continue;
+            const int cx = lx + 1, cy = ly + 1;
+            const double r = sr[cy][cx], ux = sux[cy][cx], uy = suy[cy][cx];
+            acc[0] += r;
+            acc[1] += r * ux;
+            acc[2] += r * uy;
+            const double ke = 0.5 * (ux * ux + uy * uy);
+            acc[3] += ke;
+            acc[4] += ke * ke;
+            const double w = 0.5 * (suy[cy][cx + 1] - suy[cy][cx - 1]) - 0.5 * (sux[cy + 1][cx] - sux[cy - 1][cx]);
+            const double zz = 0.5 * w * w;
+            acc[5] += zz;
+            acc[6] += zz * zz;
+            double f[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const int ai = i % 3 - 1, bi = i / 3 - 1;
+                int sx = x - ai, sy = y - bi;
+                sx = sx < 0 ? sx + a.nx : (sx >= a.nx ? sx - a.nx : sx);
+                sy = sy < 0 ? sy + a.ny : (sy >= a.ny ? sy - a.ny : sy);
+                f[i] = C::to_f64(src[(long long)i * a.plane + (long long)sy * a.nx + sx], i, a.cs);
+            }
+            double rr;
+            bool hit;
+            const double g = collide_node<VAR>(f, p, rr, hit);
+            acc[7] += g;
+            acc[8] = fmin(acc[8], g);
+            acc[9] = fmax(acc[9], g);
+        }
     }
     __shared__ double sm[kDiagParts][kDiagBlock];
 #pragma unroll
@@ -552,44 +568,51 @@ diag_partial(const typename C::S* __restrict__ src, double* __restrict__ part, S
 constexpr int kDiagExtParts = 4;
 
 template <class C>
-__device__ __forceinline__ double node_w(const typename C::S* __restrict__ src, int x, int y,
-                                         const StepArgs& a)
-{
-    auto idx = [&](int xx, int yy) -> long long {
-        xx = xx < 0 ? xx + a.nx : (xx >= a.nx ? xx - a.nx : xx);
-        yy = yy < 0 ? yy + a.ny : (yy >= a.ny ? yy - a.ny : yy);
-        return (long long)yy * a.nx + xx;
-    };
-    double r, uxp, uyp, uxm, uym, uxn, uyn, uxs, uys;
-    node_macro<C>(src, idx(x + 1, y), a, r, uxp, uyp);
-    node_macro<C>(src, idx(x - 1, y), a, r, uxm, uym);
-    node_macro<C>(src, idx(x, y + 1), a, r, uxn, uyn);
-    node_macro<C>(src, idx(x, y - 1), a, r, uxs, uys);
-    return 0.5 * (uyp - uym) - 0.5 * (uxn - uxs);
-}
-
-template <class C>
 __global__ void __launch_bounds__(kDiagBlock)
 diag_ext_partial(const typename C::S* __restrict__ src, double* __restrict__ part, StepArgs a)
 {
-    const long long total = (long long)a.nx * a.ny;
+    // u on the tile with a two-node halo, w on the tile with a one-node halo
+    constexpr int UW = kTileW + 4, UH = kTileH + 4, WW = kTileW + 2, WH = kTileH + 2;
+    __shared__ double sux[UH][UW], suy[UH][UW], sw[WH][WW];
     double acc[kDiagExtParts] = {0, 0, 0, 0};
-    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < total;
-         n += (long long)gridDim.x * blockDim.x) {
-        const int y = (int)(n / a.nx), x = (int)(n - (long long)y * a.nx);
-        const double wx = 0.5 * (node_w<C>(src, x + 1, y, a) - node_w<C>(src, x - 1, y, a));
-        const double wy = 0.5 * (node_w<C>(src, x, y + 1, a) - node_w<C>(src, x, y - 1, a));
-        const double pp = 0.5 * (wx * wx + wy * wy);
-        acc[0] += pp;
-        acc[1] += pp * pp;
-        double se = 0.0;
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            const double d = C::to_f64(src[(long long)i * a.plane + n], i, a.cs);
-            se -= (wgt(i) + d) * log1p(d * inv_wgt(i));
+    const int ntx = (a.nx + kTileW - 1) / kTileW, nty = (a.ny + kTileH - 1) / kTileH;
+    const long long ntiles = (long long)ntx * nty;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int x0 = (int)(tile % ntx) * kTileW, y0 = (int)(tile / ntx) * kTileH;
+        __syncthreads();
+        for (int q = threadIdx.x; q < UH * UW; q += blockDim.x) {
+            const int qy = q / UW, qx = q - qy * UW;
+            const int gx = wrap_mod(x0 + qx - 2, a.nx), gy = wrap_mod(y0 + qy - 2, a.ny);
+            double r;
+            node_macro<C>(src, (long long)gy * a.nx + gx, a, r, sux[qy][qx], suy[qy][qx]);
         }
-        acc[2] += se;
-        acc[3] += se * se;
+        __syncthreads();
+        // w = d uy/dx - d ux/dy by central differences
+        for (int q = threadIdx.x; q < WH * WW; q += blockDim.x) {
+            const int qy = q / WW, qx = q - qy * WW, cy = qy + 1, cx = qx + 1;
+            sw[qy][qx] = 0.5 * (suy[cy][cx + 1] - suy[cy][cx - 1]) - 0.5 * (sux[cy + 1][cx] - sux[cy - 1][cx]);
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < kTileW * kTileH; k += blockDim.x) {
+            const int ly = k / kTileW, lx = k - ly * kTileW;
+            const int x = x0 + lx, y = y0 + ly;
+            if (x >= a.nx || y >= a.ny) continue;
+            const int cx = lx + 1, cy = ly + 1;
+            const double wx = 0.5 * (sw[cy][cx + 1] - sw[cy][cx - 1]);
+            const double wy = 0.5 * (sw[cy + 1][cx] - sw[cy - 1][cx]);
+            const double pp = 0.5 * (wx * wx + wy * wy);
+            acc[0] += pp;
+            acc[1] += pp * pp;
+            const long long n = (long long)y * a.nx + x;
+            double se = 0.0;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const double d = C::to_f64(src[(long long)i * a.plane + n], i, a.cs);
+                se -= (wgt(i) + d) * log1p(d * inv_wgt(i));
+            }
+            acc[2] += se;
+            acc[3] += se * se;
+        }
     }
     __shared__ double sm[kDiagExtParts][kDiagBlock];
 #pragma unroll
