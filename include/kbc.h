@@ -222,6 +222,26 @@ int kbc_diagnostics(kbc_handle h, double* out);
  *   [3] spatial std of s */
 int kbc_diagnostics_ext(kbc_handle h, double* out);
 
+/* Shell-averaged energy and enstrophy spectra of a square periodic velocity
+ * field (the spectra of the paper's two-dimensional turbulence figures).
+ * With u_hat the discrete Fourier coefficients of u normalised by the node
+ * count, E(k) = sum over wavevectors with round(|k|) = k of |u_hat|^2 / 2,
+ * so that sum_k E(k) = mean |u|^2 / 2 (Parseval), and Z(k) = (2 pi k / n)^2
+ * E(k) (the paper's Z(k) = k^2 E(k)).
+ *   n: grid size (nx = ny = n, even, n^2 < 2^31).  u: [2][n][n] doubles,
+ *   host or device (e.g. from kbc_moments).  E, Z: nbins doubles each,
+ *   host or device; shells k >= nbins are left out (all fit when nbins >=
+ *   round(n sqrt(2) / 2) + 1).  stream: CUDA stream (NULL: the legacy
+ *   default stream); the call synchronises it before returning.
+ * The FFT is cuFFT (a library step); the binning is this library's kernel.
+ * Its shell sums use atomic additions, so their last bits depend on the
+ * order of the additions.  Device scratch (the velocity staging for host
+ * input, the half spectrum, cuFFT's work area) comes from the allocator set
+ * with kbc_set_allocator (default cudaMalloc) and is released before the
+ * call returns.  Errors: KBC_ERR_ARG, KBC_ERR_NOMEM, KBC_ERR_CUDA (message:
+ * kbc_last_error(NULL)). */
+int kbc_spectrum(int n, const double* u, int nbins, double* E, double* Z, void* stream);
+
 /* Diagnostics of a caller-owned population field without any device
  * allocation.  The paper has no counterpart to this call.
  *

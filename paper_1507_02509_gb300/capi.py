@@ -56,6 +56,7 @@ SIGNATURES = {
     "kbc_moments": (_i, [_vp, _vp, _vp]),
     "kbc_diagnostics": (_i, [_vp, _vp]),
     "kbc_diagnostics_ext": (_i, [_vp, _vp]),
+    "kbc_spectrum": (_i, [_i, _vp, _i, _vp, _vp, _vp]),
     "kbc_diagnostics_noalloc": (_i, [_i, _i, _i, _d, _vp, _vp, _vp]),
     "kbc_adjoint": (_i, [_vp, _vp, _vp, _i, _i, _i, _vp, ctypes.POINTER(_d), _vp,
                          ctypes.POINTER(_d)]),
@@ -201,6 +202,11 @@ def kbc_diagnostics(h, out):
 
 def kbc_diagnostics_ext(h, out):
     return check(h, load().kbc_diagnostics_ext(h, ptr(out)))
+
+
+def kbc_spectrum(n: int, u, nbins: int, E, Z, stream=None):
+    return check(None, load().kbc_spectrum(int(n), ptr(u), int(nbins), ptr(E), ptr(Z),
+                                           ptr(stream)))
 
 
 def kbc_diagnostics_noalloc(nx: int, ny: int, variant: int, beta: float, f, out,

@@ -10,8 +10,11 @@
 #include <thread>
 #include <vector>
 
+#include <cufft.h>
+
 #include "../../include/kbc.h"
 #include "kbc_launch.cuh"
+#include "kbc_spectrum.cuh"
 
 namespace kbc {
 
@@ -1216,6 +1219,97 @@ int kbc_bytes_per_update(kbc_handle h, double* bytes)
 {
     if (!h || !bytes) return KBC_ERR_ARG;
     *bytes = 18.0 * (double)h->elem;
+    return KBC_OK;
+}
+
+int kbc_spectrum(int n, const double* u, int nbins, double* E, double* Z, void* stream)
+{
+    if (n < 2 || n % 2 != 0 || (long long)n * n > 2147483647LL)
+        return fail(nullptr, KBC_ERR_ARG, "spectrum: n must be even, 2 <= n, n^2 < 2^31");
+    if (nbins < 1 || !u || !E || !Z) return fail(nullptr, KBC_ERR_ARG, "spectrum: bad argument");
+    Allocator al;
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        al = g_alloc;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // scratch owned by this call (the handle-free form of CallBuffers)
+    struct Scratch {
+        Allocator al;
+        cudaStream_t s;
+        void* p[4] = {nullptr, nullptr, nullptr, nullptr};
+        int k = 0;
+        cufftHandle plan = 0;
+        bool planned = false;
+        void* get(size_t bytes)
+        {
+            if (bytes == 0) bytes = 256;
+            void* q = nullptr;
+            if (al.alloc) q = al.alloc(bytes, (void*)s, al.user);
+            else if (cudaMalloc(&q, bytes) != cudaSuccess) {
+                cudaGetLastError();
+                q = nullptr;
+            }
+            if (q) p[k++] = q;
+            return q;
+        }
+        ~Scratch()
+        {
+            cudaStreamSynchronize(s);
+            if (planned) cufftDestroy(plan);
+            for (int j = 0; j < k; ++j) {
+                if (al.release) al.release(p[j], (void*)s, al.user);
+                else cudaFree(p[j]);
+            }
+            cudaGetLastError();
+        }
+    } sc{al, s};
+    const size_t nn = (size_t)n * n;
+    const double* du = u;
+    if (!is_device_ptr(u)) {
+        double* st = static_cast<double*>(sc.get(2 * nn * sizeof(double)));
+        if (!st) return fail(nullptr, KBC_ERR_NOMEM, "spectrum: staging allocation failed");
+        cudaError_t e = cudaMemcpyAsync(st, u, 2 * nn * sizeof(double), cudaMemcpyDefault, s);
+        if (e != cudaSuccess) return cuda_fail(nullptr, e, "spectrum: upload");
+        du = st;
+    }
+    double2* uh = static_cast<double2*>(sc.get((size_t)n * (n / 2 + 1) * sizeof(double2)));
+    double* acc = static_cast<double*>(sc.get(2 * (size_t)nbins * sizeof(double)));
+    if (!uh || !acc) return fail(nullptr, KBC_ERR_NOMEM, "spectrum: scratch allocation failed");
+    // cuFFT (a library step) with its work area from the same allocator
+    size_t ws = 0;
+    if (cufftCreate(&sc.plan) != CUFFT_SUCCESS) return fail(nullptr, KBC_ERR_CUDA, "spectrum: cufftCreate");
+    sc.planned = true;
+    if (cufftSetAutoAllocation(sc.plan, 0) != CUFFT_SUCCESS ||
+        cufftMakePlan2d(sc.plan, n, n, CUFFT_D2Z, &ws) != CUFFT_SUCCESS)
+        return fail(nullptr, KBC_ERR_CUDA, "spectrum: cuFFT plan");
+    void* work = sc.get(ws);
+    if (!work) return fail(nullptr, KBC_ERR_NOMEM, "spectrum: cuFFT work area allocation failed");
+    if (cufftSetWorkArea(sc.plan, work) != CUFFT_SUCCESS || cufftSetStream(sc.plan, s) != CUFFT_SUCCESS)
+        return fail(nullptr, KBC_ERR_CUDA, "spectrum: cuFFT work area / stream");
+    cudaError_t e = cudaMemsetAsync(acc, 0, (size_t)nbins * sizeof(double), s);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "spectrum: memset");
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t smem = (size_t)nbins * sizeof(double);
+    const int use_smem = smem <= (size_t)160 * 1024 ? 1 : 0;
+    if (use_smem && smem > 48 * 1024)
+        cudaFuncSetAttribute(spectrum_bin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const double scale = 1.0 / ((double)nn * (double)nn);
+    for (int c = 0; c < 2; ++c) {
+        if (cufftExecD2Z(sc.plan, const_cast<double*>(du) + c * nn, reinterpret_cast<cufftDoubleComplex*>(uh)) !=
+            CUFFT_SUCCESS)
+            return fail(nullptr, KBC_ERR_CUDA, "spectrum: cuFFT execution");
+        spectrum_bin<<<sms * 4, 256, use_smem ? smem : 0, s>>>(uh, n, nbins, scale, acc, use_smem);
+    }
+    spectrum_enstrophy<<<(nbins + 255) / 256, 256, 0, s>>>(acc, acc + nbins, nbins, n);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(E, acc, (size_t)nbins * sizeof(double), cudaMemcpyDefault, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(Z, acc + nbins, (size_t)nbins * sizeof(double), cudaMemcpyDefault, s);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "spectrum");
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "spectrum");
     return KBC_OK;
 }
 

@@ -486,6 +486,33 @@ def test_spectra_match_oracle():
     assert np.allclose(Z.cpu().numpy(), Zo, rtol=1e-10, atol=1e-22)
 
 
+def test_spectrum_entry_point_host_device_and_parseval():
+    """kbc_spectrum through the C ABI: host and device velocity give the same
+    shell sums (up to the order of the atomic additions), the shells sum to
+    mean |u|^2 / 2 (Parseval) on a 1024^2 turbulent field, and an odd n is
+    rejected."""
+    from paper_1507_02509_gb300.spectra import shell_count
+
+    n = 1024
+    _, ux, uy = flows.turbulence(n, k0=16, urms=0.03, seed=4)
+    u = np.ascontiguousarray(np.stack((ux, uy)))
+    nb = shell_count(n)
+    E_h, Z_h = np.empty(nb), np.empty(nb)
+    capi.kbc_spectrum(n, u, nb, E_h, Z_h)
+    du = torch.as_tensor(u, device="cuda")
+    E_d = torch.empty(nb, dtype=torch.float64, device="cuda")
+    Z_d = torch.empty(nb, dtype=torch.float64, device="cuda")
+    capi.kbc_spectrum(n, du, nb, E_d, Z_d)
+    assert np.allclose(E_d.cpu().numpy(), E_h, rtol=1e-12, atol=1e-30)
+    assert np.allclose(Z_d.cpu().numpy(), Z_h, rtol=1e-12, atol=1e-30)
+    assert np.sum(E_h) == pytest.approx(0.5 * np.mean(ux ** 2 + uy ** 2), rel=1e-12)
+    k = np.arange(nb)
+    assert np.allclose(Z_h, (2 * math.pi * k / n) ** 2 * E_h, rtol=1e-14, atol=0)
+    with pytest.raises(KBCError) as e:
+        capi.kbc_spectrum(n - 1, u, nb, E_h, Z_h)
+    assert e.value.status == capi.KBC_ERR_ARG
+
+
 @pytest.mark.parametrize("dtype", ["f64", "f32", "f16"])
 @pytest.mark.parametrize("variant", ["lbgk", "B", "C"])
 @pytest.mark.parametrize("shape", [(64, 64), (512, 6), (37, 19)])
