@@ -491,7 +491,7 @@ def test_spectrum_entry_point_host_device_and_parseval():
     shell sums (up to the order of the atomic additions), the shells sum to
     mean |u|^2 / 2 (Parseval) on a 1024^2 turbulent field, and an odd n is
     rejected."""
-    from paper_1507_02509_gb300.spectra import shell_count
+    from paper_1507_02509_gb300.spectra import energy_spectrum, shell_count
 
     n = 1024
     _, ux, uy = flows.turbulence(n, k0=16, urms=0.03, seed=4)
@@ -511,6 +511,12 @@ def test_spectrum_entry_point_host_device_and_parseval():
     with pytest.raises(KBCError) as e:
         capi.kbc_spectrum(n - 1, u, nb, E_h, Z_h)
     assert e.value.status == capi.KBC_ERR_ARG
+    # 10240^2: 7242 shells, a 58 KB shared histogram (above the default 48 KB)
+    n = 10240
+    _, vx, vy = flows.turbulence(n, k0=16, urms=0.03, seed=4, backend="torch", device="cuda")
+    k, E, Z = energy_spectrum(vx, vy)
+    assert E.numel() == shell_count(n) == 7242
+    assert float(E.sum()) == pytest.approx(float(0.5 * (vx ** 2 + vy ** 2).mean()), rel=1e-12)
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32", "f16"])
