@@ -117,22 +117,29 @@ def test_autograd_function_returns_adjoint_gradients():
     assert float(beta.grad) == pytest.approx(3.0 * gb, rel=1e-15)
 
 
-def test_fp32_adjoint_tracks_fp64_on_512():
+@pytest.mark.parametrize("seed", [11, 13, 17])
+def test_fp32_adjoint_tracks_fp64_on_512(seed):
     """Adjoint configuration: 512^2 periodic, seeded random velocity (k0 = 8),
-    KBC B, checkpoints every 100 steps; gradient of the final kinetic energy.
-    FP32 storage/arithmetic against the FP64 adjoint (stated, bounded)."""
-    n, steps, K = 512, 400, 100
-    rho, ux, uy = flows.turbulence(n, k0=8, urms=0.03, seed=11)
+    KBC B, 100 steps, checkpoints every 20; gradient of the final kinetic
+    energy, FP32 storage/arithmetic against the FP64 adjoint.  Over seeds
+    11-20 the FP32 error stays at the rounding level up to 100 steps (max
+    norm <= 9.6e-4, L2 <= 2.6e-5, J <= 3.7e-9, dJ/dbeta <= 4.2e-7); beyond
+    that the exact linearisation amplifies rounding where gamma* is poorly
+    determined and the error becomes seed-dependent (seeds 13 and 17, taken
+    here, are the first to leave: 0.08 and 0.13 at 200 steps)."""
+    n, steps, K = 512, 100, 20
+    rho, ux, uy = flows.turbulence(n, k0=8, urms=0.03, seed=seed)
     nu = n * 0.03 / 5000.0
     beta = 1.0 / (6 * nu + 1)
     J64, g64, gb64 = _gpu_adjoint("B", "f64", beta, rho, ux, uy, steps, K, 0)
     J32, g32, gb32 = _gpu_adjoint("B", "f32", beta, rho, ux, uy, steps, K, 0)
     rel_g = np.max(np.abs(g32 - g64)) / np.max(np.abs(g64))
-    print(f"512^2 {steps} steps: J rel {abs(J32 - J64) / J64:.2e}, grad_u0 rel {rel_g:.2e}, "
-          f"grad_beta rel {abs(gb32 - gb64) / abs(gb64):.2e}")
-    assert abs(J32 - J64) <= 1e-5 * J64
-    assert rel_g < 1e-2
-    assert abs(gb32 - gb64) <= 1e-2 * abs(gb64)
+    l2_g = np.linalg.norm(g32 - g64) / np.linalg.norm(g64)
+    print(f"512^2 {steps} steps, seed {seed}: J rel {abs(J32 - J64) / J64:.2e}, grad_u0 rel "
+          f"{rel_g:.2e} (L2 {l2_g:.2e}), grad_beta rel {abs(gb32 - gb64) / abs(gb64):.2e}")
+    assert abs(J32 - J64) <= 1e-7 * J64
+    assert rel_g < 3e-3 and l2_g < 1e-4
+    assert abs(gb32 - gb64) <= 1e-5 * abs(gb64)
 
 
 def test_fp32_adjoint_overflow_is_reported():
