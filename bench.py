@@ -29,8 +29,9 @@ if ROOT not in sys.path:
 
 METRIC = "MLUPS and % of HBM roofline (FP64/FP32/FP16-store) at stated error vs FP64 oracle"
 UNIT = "MLUPS"
-WORKLOAD = ("KBC D2Q9 throughput stress: 16384^2 doubly periodic, seeded random turbulent "
-            "initial field (E(k)~k^4 exp(-2(k/16)^2), u_rms=0.03, Re=1e5)")
+def workload(n: int) -> str:
+    return (f"KBC D2Q9 {'throughput stress: ' if n == 16384 else ''}{n}^2 doubly periodic, "
+            "seeded random turbulent initial field (E(k)~k^4 exp(-2(k/16)^2), u_rms=0.03, Re=1e5)")
 DTYPE_BYTES = {"f64": 8, "f32": 4, "f16": 2}
 
 
@@ -43,6 +44,8 @@ def parse():
     p.add_argument("--n", type=int, default=16384)
     p.add_argument("--dtype", default="f32", choices=["f64", "f32", "f16"])
     p.add_argument("--variant", default="B", choices=["lbgk", "A", "B", "C", "D"])
+    p.add_argument("--kernel", default="auto", choices=["auto", "rows", "bulk", "nodes"],
+                   help="step kernel of the headline run (auto: the library's choice)")
     p.add_argument("--extras", type=int, default=1, help="also time f64/f16/LBGK (0: skip)")
     p.add_argument("--extra-steps", type=int, default=100)
     p.add_argument("--e2e", type=int, default=1)
@@ -68,6 +71,16 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
+def step_kernel_name(args) -> str:
+    """The step kernel the headline run launches; "auto" resolves as the
+    library does: the bulk-copy kernel for FP16 KBC, the vector rows
+    otherwise (every bench width is a multiple of the row vector)."""
+    k = args.kernel
+    if k == "auto":
+        k = "bulk" if args.dtype == "f16" and args.variant != "lbgk" else "rows"
+    return {"rows": "step_rows", "bulk": "step_tma", "nodes": "step_nodes"}[k]
+
+
 def kernel_source_hash() -> str:
     """Hash of the code that defines the vector-row step kernel: the lattice,
     lane and collision headers, the kernel's own section of kbc_kernels.cuh
@@ -87,9 +100,10 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def traffic_from_profile(dtype: str, n: int):
+def traffic_from_profile(kernel: str, dtype: str, n: int):
     """DRAM bytes per launch of the step kernel from the committed ncu
-    summary, scaled to n^2 nodes; None if missing or taken on other sources."""
+    summary, scaled to n^2 nodes; None if missing, taken on another kernel
+    (name, variant, storage) or on other sources."""
     path = os.path.join(ROOT, "profiles", f"kbc_step_rows_{dtype}_traffic.txt")
     if not os.path.exists(path):
         return None
@@ -100,7 +114,7 @@ def traffic_from_profile(dtype: str, n: int):
                 k, v = line.split(":", 1)
                 vals[k.strip()] = v.strip()
     try:
-        if vals.get("kernel_source_hash") != kernel_source_hash():
+        if vals.get("kernel_source_hash") != kernel_source_hash() or vals.get("kernel") != kernel:
             return None
         return float(vals["dram_bytes_per_node"]) * n * n
     except (KeyError, ValueError):
@@ -277,6 +291,7 @@ def run_ours(args):
 
     # ---- headline: default workload
     lat = Lattice(n, n, variant=args.variant, beta=beta, dtype=args.dtype)
+    lat.set_kernel(args.kernel)
     lat.init(rho, ux, uy)
     lat.step(args.warmup)
     lat.sync()
@@ -303,11 +318,12 @@ def run_ours(args):
     kernel_s = t_roof / k_roof
     peak, peak_kind = load_peaks()
     achieved = bpu * n * n / kernel_s / 1e9
-    traffic = traffic_from_profile(args.dtype, n)
+    kname = f"{step_kernel_name(args)}<{args.variant},{args.dtype}>"
+    traffic = traffic_from_profile(kname, args.dtype, n)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
                 "algorithmic_bytes": bpu * n * n, "peak_kind": peak_kind,
-                "kernel": f"step_rows<{args.variant},{args.dtype}>",
+                "kernel": kname,
                 "kernel_ms": round(kernel_s * 1e3, 4)}
 
     # ---- e2e through the C ABI with pinned host buffers
@@ -436,7 +452,7 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(t / args.steps * 1e3, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": n, "variant": args.variant,
+            "config": {"workload": workload(n), "n": n, "variant": args.variant,
                        "storage": args.dtype, "beta": beta, "nu": nu,
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": "inputs larger than L2 (A-B buffers "
@@ -476,7 +492,7 @@ def run_reference(args):
         "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "impl": "reference",
-        "config": {"workload": WORKLOAD, "n": args.n, "variant": "B", "storage": "f64",
+        "config": {"workload": workload(args.n), "n": args.n, "variant": "B", "storage": "f64",
                    "sample": f"{n}^2 periodic field of the same generator per step"},
         "cpu_baseline": {"value": round(v, 3), "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"FP64 C oracle, {n}^2 field, {args.steps} steps"},

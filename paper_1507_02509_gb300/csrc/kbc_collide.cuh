@@ -13,7 +13,8 @@
 //   ds = the population carrying the variant's shear-moment deviations and
 //        no other moment (central basis about u for A/B, natural for C/D;
 //        this is Eq. momentsD2Q9 restricted to the s group, written with the
-//        dual vectors E_pq(c) = e_p(c_x) x e_q(c_y) of the 1-D moment basis)
+//        dual vectors E_pq(c) = e_p(c_x) x e_q(c_y) of the 1-D moment basis;
+//        for A/B the central moments are first shifted to natural ones)
 //   dh = df - ds                            (k carries no deviation, Sec. 5)
 //   gamma* = 1/beta - (2 - 1/beta) <ds|dh>/<dh|dh>               (Eq. result21)
 //   f' = f - beta (2 ds + gamma dh)                    (Eq. ksh-mirror in Eq. Egeneral)
@@ -205,49 +206,58 @@ __device__ __forceinline__ L collide(L (&d)[9], const CollideParams<typename L::
         return L(2);
     } else {
         const L m11 = s08 - s26;
-        // ds = hc20 (2 E20) + hc02 (2 E02) + m11 E11 with hc = half the
-        // coefficient: A/C carry T, N, Pi (c20 = m20, c02 = m02); B/D carry N
+        // ds carries the variant's second moments c20, c02, c11 = m11 and no
+        // other moment: A/C carry T, N, Pi (c20 = m20, c02 = m02); B/D carry N
         // and Pi only, the traceless part c20 = -c02 = (m20 - m02)/2
-        L hc20, hc02;
-        if constexpr (VAR == kA || VAR == kC) {
-            hc20 = L(0.5) * m20;
-            hc02 = L(0.5) * m02;
-        } else {
-            hc20 = L(0.25) * (m20 - m02);
-            hc02 = -hc20;
-        }
         L ds[9];
         if constexpr (VAR == kA || VAR == kB) {
-            // 1-D dual vectors about c: e0(c) = (c(c-1)/2, 1-c^2, c(c+1)/2),
-            // e1(c) = (c-1/2, -2c, c+1/2), e2 = (1/2, -1, 1/2), and
-            // ds_(a,b) = c20 e2[a] e0y[b] + c02 e0x[a] e2[b] + m11 e1x[a] e1y[b]
-            const L qx = L(0.5) * uxx, hx = L(0.5) * ux;
-            const L qy = L(0.5) * uyy, hy = L(0.5) * uy;
-            const L e0x[3] = {qx - hx, L(1) - uxx, qx + hx};
-            const L e0y[3] = {qy - hy, L(1) - uyy, qy + hy};
-            const L e1x[3] = {ux - L(0.5), L(-2) * ux, ux + L(0.5)};
-            const L e1y[3] = {uy - L(0.5), L(-2) * uy, uy + L(0.5)};
-            L Y[3], X[3], M[3];  // half c20 e0y, half c02 e0x, m11 e1x
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                Y[k] = hc20 * e0y[k];
-                X[k] = hc02 * e0x[k];
-                M[k] = m11 * e1x[k];
+            // Central basis about c = u: the other central moments of ds
+            // vanish.  The binomial shift a = (a - ux) + ux turns that into
+            // natural moments (mass and momentum stay zero)
+            //   M21 = uy c20 + 2 ux c11,  M12 = ux c02 + 2 uy c11,
+            //   M22 = uy^2 c20 + ux^2 c02 + 4 ux uy c11,
+            // and the natural dual vectors e0 = (0,1,0), e1 = (-1/2,0,1/2),
+            // e2 = (1/2,-1,1/2) give the same population as the central ones
+            // e_p(c) would, in about 30 operations instead of 46.  With
+            // q = c/4 and Q = M/4:
+            //   ds(0,0) = 4 (Q22 - q20 - q02),  ds(a,0) = 2 (q20 - Q22 - a Q12),
+            //   ds(0,b) = 2 (q02 - Q22 - b Q21),
+            //   ds(a,b) = Q22 + a Q12 + b Q21 + a b q11   (a, b = +-1)
+            L q20, q02;
+            if constexpr (VAR == kA) {
+                q20 = L(0.25) * m20;
+                q02 = L(0.25) * m02;
+            } else {
+                q20 = L(0.125) * (m20 - m02);
+                q02 = -q20;
             }
-            // c20 e2[a] e0y[b] + c02 e0x[a] e2[b]: Y[b] + X[a] for a, b != 0,
-            // a factor -2 on the Y term when a = 0 and on the X term when b = 0
-#pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                const int a = i % 3, b = i / 3;  // a, b in {0,1,2} <-> {-1,0,1}
-                L t;
-                if (a != 1 && b != 1) t = Y[b] + X[a];
-                else if (a == 1 && b != 1) t = fmaL(L(-2), Y[b], X[a]);
-                else if (a != 1) t = fmaL(L(-2), X[a], Y[b]);
-                else t = L(-2) * (Y[1] + X[1]);
-                ds[i] = fmaL(M[a], e1y[b], t);
-            }
+            const L q11 = L(0.25) * m11, h11 = L(0.5) * m11;
+            const L Q21 = fmaL(ux, h11, uy * q20);
+            const L Q12 = fmaL(uy, h11, ux * q02);
+            const L Q22 = fmaL(uyy, q20, fmaL(uxx, q02, (ux * uy) * m11));
+            if constexpr (VAR == kA) ds[4] = L(4) * (Q22 - (q20 + q02));
+            else ds[4] = L(4) * Q22;  // q20 + q02 = 0
+            const L ex2 = L(2) * (q20 - Q22), ey2 = L(2) * (q02 - Q22);
+            ds[3] = fmaL(L(2), Q12, ex2);
+            ds[5] = fmaL(L(-2), Q12, ex2);
+            ds[1] = fmaL(L(2), Q21, ey2);
+            ds[7] = fmaL(L(-2), Q21, ey2);
+            const L sp = Q22 + Q12, sm = Q22 - Q12, rp = Q21 + q11, rm = Q21 - q11;
+            ds[8] = sp + rp;
+            ds[2] = sp - rp;
+            ds[6] = sm + rm;
+            ds[0] = sm - rm;
         } else {
-            // natural basis (c = 0): e0 = (0,1,0), e1 = (-1/2, 0, 1/2)
+            // natural basis (c = 0): e0 = (0,1,0), e1 = (-1/2, 0, 1/2);
+            // hc = half the coefficient
+            L hc20, hc02;
+            if constexpr (VAR == kC) {
+                hc20 = L(0.5) * m20;
+                hc02 = L(0.5) * m02;
+            } else {
+                hc20 = L(0.25) * (m20 - m02);
+                hc02 = -hc20;
+            }
             const L q = L(0.25) * m11;
             ds[4] = L(-2) * (hc20 + hc02);
             ds[3] = ds[5] = hc20;
