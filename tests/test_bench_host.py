@@ -38,3 +38,34 @@ def test_reference_arm_json_line():
 def test_reference_arm_other_ranks_are_silent():
     r = _run({"WORLD_SIZE": "2", "RANK": "1", "LOCAL_RANK": "1"})
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_roofline_kernel_name_and_traffic_record():
+    """The roofline names the kernel the headline run launches, and the
+    committed ncu traffic record applies only to that kernel on the current
+    sources."""
+    sys.path.insert(0, ROOT)
+    import argparse
+
+    import bench
+
+    def name(**kw):
+        a = argparse.Namespace(**{"kernel": "auto", "dtype": "f32", "variant": "B", **kw})
+        return bench.step_kernel_name(a)
+
+    assert name() == "step_rows"
+    assert name(dtype="f16") == "step_tma"
+    assert name(dtype="f16", variant="lbgk") == "step_rows"
+    assert name(kernel="rows", dtype="f16") == "step_rows"
+    assert name(kernel="bulk") == "step_tma" and name(kernel="nodes") == "step_nodes"
+    n = 16384
+    t = bench.traffic_from_profile("step_rows<B,f32>", "f32", n)
+    with open(os.path.join(ROOT, "profiles", "kbc_step_rows_f32_traffic.txt")) as f:
+        current = f"kernel_source_hash: {bench.kernel_source_hash()}" in f.read()
+    if current:
+        assert t is not None and 70 * n * n < t <= 72 * n * n
+    else:  # sources changed since the capture: no stale figure is reported
+        assert t is None
+    assert bench.traffic_from_profile("step_rows<C,f32>", "f32", n) is None
+    assert bench.traffic_from_profile("step_tma<B,f32>", "f32", n) is None
+    assert bench.traffic_from_profile("step_tma<B,f16>", "f16", n) is None
