@@ -217,12 +217,17 @@ StepArgs args_of(const kbc_ctx* h)
     a.nx = h->nx;
     a.ny = h->ny;
     a.plane = h->plane;
-    a.cs.scale = h->f16_scale;
-    a.cs.inv_scale = 1.0f / h->f16_scale;
+    a.cs = make_scale(h->f16_scale);
     const int fixed = (h->gamma_mode == KBC_GAMMA_FIXED) ? 1 : (h->gamma_mode == KBC_GAMMA_EXACT ? 2 : 0);
     const double guard = (h->dtype == KBC_F64) ? 0.0 : h->guard;
     a.pf = make_params<float>(h->beta, fixed, h->gamma_fixed, guard);
     a.pd = make_params<double>(h->beta, fixed, h->gamma_fixed, guard);
+    if (h->dtype == KBC_F16_DEV) {  // the FP16 step kernels collide in storage units
+        const double s = h->f16_scale, c = 1.0 / (36.0 * s);
+        a.pf.unit_s = (float)s;
+        a.pf.unit_c = (float)c;
+        a.pf.guard_u = (float)(guard / (c * c));
+    }
     a.beta = h->beta;
     a.fix_count = h->fix;
     a.fix_list = h->fix ? h->fix + 64 : nullptr;

@@ -44,6 +44,9 @@ struct CollideParams {
     T ch_fixed;        // beta (gamma_fixed - 2)
     T gamma_fixed;
     T guard;           // threshold on rho <dh|dh>; <= 0 disables
+    T unit_s;          // storage units (FP16): S, with d_i = e_i W_i / S
+    T unit_c;          // 1 / (36 S), the unit of the diagonal populations
+    T guard_u;         // the guard threshold in those units, guard (36 S)^2
     int fixed;         // 1: gamma = gamma_fixed
     int exact;         // 1: gamma from the root of Eq. result1 (double arithmetic only)
 };
@@ -59,6 +62,9 @@ __host__ inline CollideParams<T> make_params(double beta, int fixed, double gamm
     p.ch_fixed = (T)(beta * (gamma_fixed - 2.0));
     p.gamma_fixed = (T)gamma_fixed;
     p.guard = (T)guard;
+    p.unit_s = (T)1;
+    p.unit_c = (T)1;
+    p.guard_u = (T)guard;
     p.fixed = fixed == 1 ? 1 : 0;
     p.exact = fixed == 2 ? 1 : 0;
     return p;
@@ -91,11 +97,19 @@ __device__ __forceinline__ L eq_poly(L ux, L uy, L sxy, L dxy, L nusq15)
     }
 }
 
-// df_i = d_i - (f^eq_i - W_i), with f^eq - W = W (rho - 1 + rho P)
-template <int I, class L>
-__device__ __forceinline__ L neq(L d, L rho, L drho, L P)
+// storage-unit multiplicity m_i = 36 W_i: 1 (diagonal), 4 (axis), 16 (rest)
+__host__ __device__ constexpr double unit_m(int i)
 {
-    return fmaL(L(-wgt(I)), fmaL(rho, P, drho), d);
+    return (va(i) != 0 && vb(i) != 0) ? 1.0 : (va(i) == 0 && vb(i) == 0) ? 16.0 : 4.0;
+}
+
+// df_i = d_i - (f^eq_i - W_i), with f^eq - W = W (rho - 1 + rho P); in
+// storage units (d_i = e_i W_i / S) the factor W_i becomes S for every i
+template <int I, bool U, class L>
+__device__ __forceinline__ L neq(L d, L rho, L drho, L P, L unit_s)
+{
+    if constexpr (U) return fmaL(-unit_s, fmaL(rho, P, drho), d);
+    else return fmaL(L(-wgt(I)), fmaL(rho, P, drho), d);
 }
 
 // Montgomery's simultaneous inversion: w_i = 1 / x_i for nine x_i with one
@@ -158,18 +172,45 @@ __device__ __forceinline__ double exact_gamma(const double (&ds)[9], const doubl
 // three follow from sum df = sum a df = sum b df = 0 (the collision
 // conserves rho and rho u).  The rounding of f^eq (about eps |f^eq - W|)
 // then never leaks into the conserved moments, where nothing would damp it.
-template <int VAR, class L>
+//
+// U (storage units, FP16 only): d_i holds e_i = (f_i - W_i) S / W_i, the
+// half-precision code itself, and so do df, ds, dh and the result.  With
+// c = 1/(36 S) the deviation is c m_i e_i, m_i = 36 W_i = 1, 4, 16 (diagonal,
+// axis, rest), exact powers of two: the moment sums weight e_i by m_i, the
+// second moments and ds come out in units of c and are divided by m_i in
+// their constants, and the entropic weights become m_i^2 rho / f^eq_i, which
+// scales <ds|dh> and <dh|dh> alike by 1/c^2 (the guard threshold with them).
+// The codec then needs no multiplication on either side.
+template <int VAR, class L, bool U = false>
 __device__ __forceinline__ L collide(L (&d)[9], const CollideParams<typename L::S>& p, L& rho_out,
                                      unsigned& guard_hits)
 {
-    // column sums (a = +1, -1, 0) and row sums (b = +1, -1)
-    const L cR = (d[2] + d[5]) + d[8], cL = (d[0] + d[3]) + d[6], cM = (d[1] + d[4]) + d[7];
-    const L rT = (d[6] + d[7]) + d[8], rB = (d[0] + d[1]) + d[2];
-    const L drho = (cR + cL) + cM;
-    const L jx = cR - cL, jy = rT - rB;
+    constexpr bool dbl = std::is_same<typename L::S, double>::value;
+    static_assert(!(U && dbl), "storage units are a single-precision path");
+    // column sums (a = +1, -1, 0) and row sums (b = +1, -1); in units, cM is
+    // a quarter of the middle column
+    L cR, cL, cM, rT, rB, drho, jx, jy;
+    if constexpr (U) {
+        cR = fmaL(L(4), d[5], d[2] + d[8]);
+        cL = fmaL(L(4), d[3], d[0] + d[6]);
+        cM = fmaL(L(4), d[4], d[1] + d[7]);
+        rT = fmaL(L(4), d[7], d[6] + d[8]);
+        rB = fmaL(L(4), d[1], d[0] + d[2]);
+        drho = L(p.unit_c) * fmaL(L(4), cM, cR + cL);
+    } else {
+        cR = (d[2] + d[5]) + d[8];
+        cL = (d[0] + d[3]) + d[6];
+        cM = (d[1] + d[4]) + d[7];
+        rT = (d[6] + d[7]) + d[8];
+        rB = (d[0] + d[1]) + d[2];
+        drho = (cR + cL) + cM;
+    }
+    jx = cR - cL;
+    jy = rT - rB;
     const L rho = L(1) + drho;
     rho_out = rho;
-    const L irho = rcp_fast(rho);
+    L irho = rcp_fast(rho);
+    if constexpr (U) irho = irho * L(p.unit_c);  // j is in units of c
     const L ux = jx * irho, uy = jy * irho;
     const L uxx = ux * ux, uyy = uy * uy;
     const L nusq15 = L(-1.5) * (uxx + uyy);
@@ -182,21 +223,35 @@ __device__ __forceinline__ L collide(L (&d)[9], const CollideParams<typename L::
     P[3] = eq_poly<3>(ux, uy, sxy, dxy, nusq15);
     P[6] = eq_poly<6>(ux, uy, sxy, dxy, nusq15);
     P[8] = eq_poly<8>(ux, uy, sxy, dxy, nusq15);
-    df[0] = neq<0>(d[0], rho, drho, P[0]);
-    df[1] = neq<1>(d[1], rho, drho, P[1]);
-    df[2] = neq<2>(d[2], rho, drho, P[2]);
-    df[3] = neq<3>(d[3], rho, drho, P[3]);
-    df[6] = neq<6>(d[6], rho, drho, P[6]);
-    df[8] = neq<8>(d[8], rho, drho, P[8]);
-    df[5] = (df[3] - (df[2] + df[8])) + (df[0] + df[6]);  // sum a df = 0
-    df[7] = (df[1] - (df[6] + df[8])) + (df[0] + df[2]);  // sum b df = 0
+    const L us(p.unit_s);
+    df[0] = neq<0, U>(d[0], rho, drho, P[0], us);
+    df[1] = neq<1, U>(d[1], rho, drho, P[1], us);
+    df[2] = neq<2, U>(d[2], rho, drho, P[2], us);
+    df[3] = neq<3, U>(d[3], rho, drho, P[3], us);
+    df[6] = neq<6, U>(d[6], rho, drho, P[6], us);
+    df[8] = neq<8, U>(d[8], rho, drho, P[8], us);
     // second moments of df; df carries no mass or momentum, so its central
     // and natural second moments coincide (see header)
-    const L s08 = df[0] + df[8], s26 = df[2] + df[6];
-    const L corner = s08 + s26, s17 = df[1] + df[7];
-    const L m20 = corner + (df[3] + df[5]);
-    const L m02 = corner + s17;
-    df[4] = -(m20 + s17);                                 // sum df = 0
+    L m20, m02, s08, s26;
+    if constexpr (U) {
+        df[5] = fmaL(L(0.25), (df[0] + df[6]) - (df[2] + df[8]), df[3]);  // sum a m df = 0
+        df[7] = fmaL(L(0.25), (df[0] + df[2]) - (df[6] + df[8]), df[1]);  // sum b m df = 0
+        s08 = df[0] + df[8];
+        s26 = df[2] + df[6];
+        const L corner = s08 + s26, s17 = df[1] + df[7];
+        m20 = fmaL(L(4), df[3] + df[5], corner);
+        m02 = fmaL(L(4), s17, corner);
+        df[4] = L(-0.0625) * fmaL(L(4), s17, m20);                      // sum m df = 0
+    } else {
+        df[5] = (df[3] - (df[2] + df[8])) + (df[0] + df[6]);  // sum a df = 0
+        df[7] = (df[1] - (df[6] + df[8])) + (df[0] + df[2]);  // sum b df = 0
+        s08 = df[0] + df[8];
+        s26 = df[2] + df[6];
+        const L corner = s08 + s26, s17 = df[1] + df[7];
+        m20 = corner + (df[3] + df[5]);
+        m02 = corner + s17;
+        df[4] = -(m20 + s17);                                 // sum df = 0
+    }
 
     const L n2b(-p.two_beta);
     if constexpr (VAR == kLBGK) {
@@ -223,6 +278,9 @@ __device__ __forceinline__ L collide(L (&d)[9], const CollideParams<typename L::
             //   ds(0,0) = 4 (Q22 - q20 - q02),  ds(a,0) = 2 (q20 - Q22 - a Q12),
             //   ds(0,b) = 2 (q02 - Q22 - b Q21),
             //   ds(a,b) = Q22 + a Q12 + b Q21 + a b q11   (a, b = +-1)
+            // (in storage units the centre and edge factors are divided by
+            // m = 16 and 4)
+            constexpr double kc = U ? 0.25 : 4.0, ke = U ? 0.5 : 2.0;
             L q20, q02;
             if constexpr (VAR == kA) {
                 q20 = L(0.25) * m20;
@@ -235,13 +293,13 @@ __device__ __forceinline__ L collide(L (&d)[9], const CollideParams<typename L::
             const L Q21 = fmaL(ux, h11, uy * q20);
             const L Q12 = fmaL(uy, h11, ux * q02);
             const L Q22 = fmaL(uyy, q20, fmaL(uxx, q02, (ux * uy) * m11));
-            if constexpr (VAR == kA) ds[4] = L(4) * (Q22 - (q20 + q02));
-            else ds[4] = L(4) * Q22;  // q20 + q02 = 0
-            const L ex2 = L(2) * (q20 - Q22), ey2 = L(2) * (q02 - Q22);
-            ds[3] = fmaL(L(2), Q12, ex2);
-            ds[5] = fmaL(L(-2), Q12, ex2);
-            ds[1] = fmaL(L(2), Q21, ey2);
-            ds[7] = fmaL(L(-2), Q21, ey2);
+            if constexpr (VAR == kA) ds[4] = L(kc) * (Q22 - (q20 + q02));
+            else ds[4] = L(kc) * Q22;  // q20 + q02 = 0
+            const L ex2 = L(ke) * (q20 - Q22), ey2 = L(ke) * (q02 - Q22);
+            ds[3] = fmaL(L(ke), Q12, ex2);
+            ds[5] = fmaL(L(-ke), Q12, ex2);
+            ds[1] = fmaL(L(ke), Q21, ey2);
+            ds[7] = fmaL(L(-ke), Q21, ey2);
             const L sp = Q22 + Q12, sm = Q22 - Q12, rp = Q21 + q11, rm = Q21 - q11;
             ds[8] = sp + rp;
             ds[2] = sp - rp;
@@ -249,17 +307,19 @@ __device__ __forceinline__ L collide(L (&d)[9], const CollideParams<typename L::
             ds[0] = sm - rm;
         } else {
             // natural basis (c = 0): e0 = (0,1,0), e1 = (-1/2, 0, 1/2);
-            // hc = half the coefficient
+            // hc = half the coefficient (a quarter of that in storage units,
+            // where the edges are divided by m = 4 and the centre by 16)
+            constexpr double kh = U ? 0.25 : 1.0;
             L hc20, hc02;
             if constexpr (VAR == kC) {
-                hc20 = L(0.5) * m20;
-                hc02 = L(0.5) * m02;
+                hc20 = L(0.5 * kh) * m20;
+                hc02 = L(0.5 * kh) * m02;
             } else {
-                hc20 = L(0.25) * (m20 - m02);
+                hc20 = L(0.25 * kh) * (m20 - m02);
                 hc02 = -hc20;
             }
             const L q = L(0.25) * m11;
-            ds[4] = L(-2) * (hc20 + hc02);
+            ds[4] = L(U ? -0.5 : -2.0) * (hc20 + hc02);
             ds[3] = ds[5] = hc20;
             ds[1] = ds[7] = hc02;
             ds[0] = ds[8] = q;
@@ -270,8 +330,10 @@ __device__ __forceinline__ L collide(L (&d)[9], const CollideParams<typename L::
         P[7] = eq_poly<7>(ux, uy, sxy, dxy, nusq15);
         L x[9], w[9];
 #pragma unroll
-        for (int i = 0; i < 9; ++i) x[i] = fmaL(L(wgt(i)), P[i], L(wgt(i)));  // f^eq_i / rho
-        constexpr bool dbl = std::is_same<typename L::S, double>::value;
+        for (int i = 0; i < 9; ++i) {  // f^eq_i / rho (over m_i^2 in storage units)
+            const double wx = U ? 1.0 / (36.0 * unit_m(i)) : wgt(i);  // W_i / m_i^2
+            x[i] = fmaL(L(wx), P[i], L(wx));
+        }
         L xprod;  // double lanes: prod_i x_i, the common factor of their weights
         if constexpr (dbl) {
             // gamma* uses the weights only through <ds|dh> / <dh|dh>, which a
@@ -314,7 +376,8 @@ __device__ __forceinline__ L collide(L (&d)[9], const CollideParams<typename L::
             gamma = L(p.gamma_fixed);
         } else {
             // the guard concerns single precision (double lanes never flag)
-            if (!dbl && p.guard > 0) guard_hits = ~gt_mask(hh, L(p.guard)) & ((1u << L::kLanes) - 1u);
+            const typename L::S gthr = U ? p.guard_u : p.guard;
+            if (!dbl && gthr > 0) guard_hits = ~gt_mask(hh, L(gthr)) & ((1u << L::kLanes) - 1u);
             // <dh|dh> = 0 means dh = 0: gamma multiplies nothing; report 2
             // (double lanes: the sign of <dh|dh> is that of hh * prod x)
             unsigned pos;
@@ -346,8 +409,9 @@ __device__ __forceinline__ L collide(L (&d)[9], const CollideParams<typename L::
     }
 }
 
-// One node in float or double (wraps the scalar into its lane type).
-template <int VAR, typename T>
+// One node in float or double (wraps the scalar into its lane type); U:
+// f holds storage units (see collide).
+template <int VAR, bool U = false, typename T>
 __device__ __forceinline__ T collide_node(T (&f)[9], const CollideParams<T>& p, T& rho, bool& hit)
 {
     using L = typename LaneOf<T>::type;
@@ -356,7 +420,7 @@ __device__ __forceinline__ T collide_node(T (&f)[9], const CollideParams<T>& p, 
     for (int i = 0; i < 9; ++i) d[i] = L(f[i]);
     L r;
     unsigned h;
-    const L g = collide<VAR>(d, p, r, h);
+    const L g = collide<VAR, L, U>(d, p, r, h);
 #pragma unroll
     for (int i = 0; i < 9; ++i) f[i] = d[i].v;
     rho = r.v;

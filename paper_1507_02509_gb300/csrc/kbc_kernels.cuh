@@ -123,7 +123,7 @@ __device__ __forceinline__ void record_fix_mask(unsigned hits, int n0, const Ste
 
 // Collides the NV nodes one thread holds.  Sets `bad` when a density is not
 // finite; bit k of the result marks a guard hit of node k.
-template <int VAR, typename T, int NV>
+template <int VAR, bool U, typename T, int NV>
 __device__ __forceinline__ unsigned collide_vec(T (&f)[NV][9], const CollideParams<T>& p, bool& bad)
 {
     unsigned hits = 0u;
@@ -131,7 +131,7 @@ __device__ __forceinline__ unsigned collide_vec(T (&f)[NV][9], const CollidePara
     for (int k = 0; k < NV; ++k) {
         T rho;
         bool hit;
-        collide_node<VAR>(f[k], p, rho, hit);
+        collide_node<VAR, U>(f[k], p, rho, hit);
         bad |= !isfinite(rho);
         hits |= (hit ? 1u : 0u) << k;
     }
@@ -187,23 +187,23 @@ step_rows(const typename C::S* __restrict__ src, typename C::S* __restrict__ dst
         const int ai = i % 3 - 1;
         if (ai == 0) {
 #pragma unroll
-            for (int k = 0; k < NV; ++k) f[k][i] = C::decode(raw[i][k], i, a.cs);
+            for (int k = 0; k < NV; ++k) f[k][i] = C::load(raw[i][k], i, a.cs);
         } else if (ai == 1) {  // source x - 1
             S left = shfl_up1(raw[i][NV - 1]);
             if (lane == 0) left = edge[i];
-            f[0][i] = C::decode(left, i, a.cs);
+            f[0][i] = C::load(left, i, a.cs);
 #pragma unroll
-            for (int k = 1; k < NV; ++k) f[k][i] = C::decode(raw[i][k - 1], i, a.cs);
+            for (int k = 1; k < NV; ++k) f[k][i] = C::load(raw[i][k - 1], i, a.cs);
         } else {               // source x + 1
             S right = shfl_down1(raw[i][0]);
             if (lane == 31) right = edge[i];
 #pragma unroll
-            for (int k = 0; k < NV - 1; ++k) f[k][i] = C::decode(raw[i][k + 1], i, a.cs);
-            f[NV - 1][i] = C::decode(right, i, a.cs);
+            for (int k = 0; k < NV - 1; ++k) f[k][i] = C::load(raw[i][k + 1], i, a.cs);
+            f[NV - 1][i] = C::load(right, i, a.cs);
         }
     }
     bool bad = false;
-    const unsigned hits = collide_vec<VAR>(f, params_of<T>(a), bad);
+    const unsigned hits = collide_vec<VAR, C::kUnits>(f, params_of<T>(a), bad);
     if constexpr (VAR != kLBGK) {
         if (a.fix_list) record_fix_mask<NV>(hits, y * a.nx + x0, a);
     }
@@ -214,12 +214,12 @@ step_rows(const typename C::S* __restrict__ src, typename C::S* __restrict__ dst
         if constexpr (std::is_same<C, CodecF16>::value && NV % 2 == 0) {
             unsigned pk[NV / 2];
 #pragma unroll
-            for (int k = 0; k < NV; k += 2) pk[k / 2] = C::encode2(f[k][i], f[k + 1][i], i, a.cs);
+            for (int k = 0; k < NV; k += 2) pk[k / 2] = C::store2(f[k][i], f[k + 1][i], i, a.cs);
             Vec<unsigned, NV / 2>::store(reinterpret_cast<unsigned*>(dst + (long long)i * a.plane + o), pk);
         } else {
             S out[NV];
 #pragma unroll
-            for (int k = 0; k < NV; ++k) out[k] = C::encode(f[k][i], i, a.cs);
+            for (int k = 0; k < NV; ++k) out[k] = C::store(f[k][i], i, a.cs);
             Vec<S, NV>::store(dst + (long long)i * a.plane + o, out);
         }
     }
@@ -247,17 +247,17 @@ step_nodes(const typename C::S* __restrict__ src, typename C::S* __restrict__ ds
             int sx = x - ai, sy = y - bi;
             sx = sx < 0 ? sx + a.nx : (sx >= a.nx ? sx - a.nx : sx);
             sy = sy < 0 ? sy + a.ny : (sy >= a.ny ? sy - a.ny : sy);
-            f[i] = C::decode(__ldg(src + (long long)i * a.plane + (long long)sy * a.nx + sx), i, a.cs);
+            f[i] = C::load(__ldg(src + (long long)i * a.plane + (long long)sy * a.nx + sx), i, a.cs);
         }
         T rho;
         bool hit;
-        collide_node<VAR>(f, p, rho, hit);
+        collide_node<VAR, C::kUnits>(f, p, rho, hit);
         if (!isfinite(rho)) *a.flag = 1;
         if constexpr (VAR != kLBGK) {
             if (a.fix_list) record_fix(hit, (int)n, a);
         }
 #pragma unroll
-        for (int i = 0; i < 9; ++i) dst[(long long)i * a.plane + n] = C::encode(f[i], i, a.cs);
+        for (int i = 0; i < 9; ++i) dst[(long long)i * a.plane + n] = C::store(f[i], i, a.cs);
     }
 }
 

@@ -28,15 +28,43 @@ template <typename T> __device__ __forceinline__ T fmaT(T a, T b, T c);
 template <> __device__ __forceinline__ float fmaT<float>(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 template <> __device__ __forceinline__ double fmaT<double>(double a, double b, double c) { return __fma_rn(a, b, c); }
 
-// Scale of the half-precision encoding (unused by the other codecs).
+// weight class of population i: 0 diagonal (W = 1/36), 1 axis (1/9), 2 rest (4/9)
+__host__ __device__ constexpr int wclass(int i)
+{
+    return (va(i) != 0 && vb(i) != 0) ? 0 : (va(i) == 0 && vb(i) == 0) ? 2 : 1;
+}
+
+// Scale of the half-precision encoding (unused by the other codecs): S and,
+// per weight class, the decode factor W/S and the encode factor S/W, each
+// rounded once on the host, so that the kernels take them from the
+// parameter bank instead of forming them per thread.
 struct CodecScale {
     float scale;      // S
     float inv_scale;  // 1 / S
+    float dec[3];     // W_c / S
+    float enc[3];     // S / W_c
 };
+
+__host__ inline CodecScale make_scale(double s)
+{
+    const double w[3] = {1.0 / 36.0, 1.0 / 9.0, 4.0 / 9.0};
+    CodecScale c;
+    c.scale = (float)s;
+    c.inv_scale = (float)(1.0 / s);
+    for (int k = 0; k < 3; ++k) {
+        c.dec[k] = (float)(w[k] / s);
+        c.enc[k] = (float)(s / w[k]);
+    }
+    return c;
+}
 
 // Storage codecs: S = stored element, T = arithmetic type.
 //   decode(s, i, c)     -> d_i = f_i - W_i in T
 //   encode(d, i, c)     -> stored element
+//   load(s, i, c), store(e, i, c)
+//                       -> the step kernels' view: the value the collision
+//                          works on, d_i itself, or with kUnits the storage
+//                          code in T (the collision's storage units)
 //   to_f64(s, i, c)     -> d_i in double (exact for F64/F32 storage)
 //   from_f64(d, i, c)   -> stored element from a double deviation
 // kVec: nodes per thread of the vector-row kernel (kVec * sizeof(S) bytes
@@ -53,8 +81,11 @@ struct CodecF64 {
     using T = double;
     static constexpr int kVec = 2;
     static constexpr int kRowMinBlocks = 1;
+    static constexpr bool kUnits = false;
     __device__ __forceinline__ static T decode(S s, int, const CodecScale&) { return s; }
     __device__ __forceinline__ static S encode(T d, int, const CodecScale&) { return d; }
+    __device__ __forceinline__ static T load(S s, int, const CodecScale&) { return s; }
+    __device__ __forceinline__ static S store(T d, int, const CodecScale&) { return d; }
     __device__ __forceinline__ static double to_f64(S s, int, const CodecScale&) { return s; }
     __device__ __forceinline__ static S from_f64(double d, int, const CodecScale&) { return d; }
 };
@@ -64,33 +95,45 @@ struct CodecF32 {
     using T = float;
     static constexpr int kVec = 4;
     static constexpr int kRowMinBlocks = 12;
+    static constexpr bool kUnits = false;
     __device__ __forceinline__ static T decode(S s, int, const CodecScale&) { return s; }
     __device__ __forceinline__ static S encode(T d, int, const CodecScale&) { return d; }
+    __device__ __forceinline__ static T load(S s, int, const CodecScale&) { return s; }
+    __device__ __forceinline__ static S store(T d, int, const CodecScale&) { return d; }
     __device__ __forceinline__ static double to_f64(S s, int, const CodecScale&) { return (double)s; }
     __device__ __forceinline__ static S from_f64(double d, int, const CodecScale&) { return __double2float_rn(d); }
 };
 
 // (f - W)/W * S in IEEE half (stored as its 16-bit pattern), arithmetic in
-// float.
+// float.  The step kernels collide in storage units: load and store are the
+// bare conversions.
 struct CodecF16 {
     using S = unsigned short;
     using T = float;
     static constexpr int kVec = 4;
     static constexpr int kRowMinBlocks = 12;
+    static constexpr bool kUnits = true;
+    __device__ __forceinline__ static T load(S s, int, const CodecScale&)
+    {
+        return __half2float(__ushort_as_half(s));
+    }
+    __device__ __forceinline__ static S store(T e, int, const CodecScale&)
+    {
+        return __half_as_ushort(__float2half_rn(e));
+    }
+    // two populations of the same plane in one packed conversion
+    __device__ __forceinline__ static unsigned store2(T e0, T e1, int, const CodecScale&)
+    {
+        const __half2 h = __floats2half2_rn(e0, e1);
+        return *reinterpret_cast<const unsigned*>(&h);
+    }
     __device__ __forceinline__ static T decode(S s, int i, const CodecScale& c)
     {
-        return __half2float(__ushort_as_half(s)) * ((float)wgt(i) * c.inv_scale);
+        return __half2float(__ushort_as_half(s)) * c.dec[wclass(i)];
     }
     __device__ __forceinline__ static S encode(T d, int i, const CodecScale& c)
     {
-        return __half_as_ushort(__float2half_rn(d * ((float)inv_wgt(i) * c.scale)));
-    }
-    // two populations of the same plane in one packed conversion
-    __device__ __forceinline__ static unsigned encode2(T d0, T d1, int i, const CodecScale& c)
-    {
-        const float k = (float)inv_wgt(i) * c.scale;
-        const __half2 h = __floats2half2_rn(d0 * k, d1 * k);
-        return *reinterpret_cast<const unsigned*>(&h);
+        return __half_as_ushort(__float2half_rn(d * c.enc[wclass(i)]));
     }
     __device__ __forceinline__ static double to_f64(S s, int i, const CodecScale& c)
     {

@@ -76,7 +76,7 @@ extern "C" int kbc_diagnostics_noalloc(int nx, int ny, int variant, double beta,
     a.nx = nx;
     a.ny = ny;
     a.plane = total;
-    a.cs.scale = a.cs.inv_scale = 1.0f;
+    a.cs = make_scale(1.0);
     a.pd = make_params<double>(beta, 0, 2.0, 0.0);
     a.pf = make_params<float>(beta, 0, 2.0, 0.0);
     a.beta = beta;

@@ -239,27 +239,27 @@ step_tma(const typename C::S* __restrict__ src, typename C::S* __restrict__ dst,
                 S v[NV];
                 lds_vec<S, NV>(pl + H + lx, v);
 #pragma unroll
-                for (int q = 0; q < NV; ++q) f[q][i] = C::decode(v[q], i, a.cs);
+                for (int q = 0; q < NV; ++q) f[q][i] = C::load(v[q], i, a.cs);
             } else if (ai == 1) {  // column x - 1
                 S lo[NV], hi[NV];
                 lds_vec<S, NV>(pl + H - NV + lx, lo);
                 lds_vec<S, NV>(pl + H + lx, hi);
-                f[0][i] = C::decode(lo[NV - 1], i, a.cs);
+                f[0][i] = C::load(lo[NV - 1], i, a.cs);
 #pragma unroll
-                for (int q = 1; q < NV; ++q) f[q][i] = C::decode(hi[q - 1], i, a.cs);
+                for (int q = 1; q < NV; ++q) f[q][i] = C::load(hi[q - 1], i, a.cs);
             } else {               // column x + 1
                 S lo[NV], hi[NV];
                 lds_vec<S, NV>(pl + H + lx, lo);
                 lds_vec<S, NV>(pl + H + NV + lx, hi);
 #pragma unroll
-                for (int q = 0; q < NV - 1; ++q) f[q][i] = C::decode(lo[q + 1], i, a.cs);
-                f[NV - 1][i] = C::decode(hi[0], i, a.cs);
+                for (int q = 0; q < NV - 1; ++q) f[q][i] = C::load(lo[q + 1], i, a.cs);
+                f[NV - 1][i] = C::load(hi[0], i, a.cs);
             }
         }
         // this warp's operands are in registers: release the stage
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
-        const unsigned hits = collide_vec<VAR>(f, p, bad);
+        const unsigned hits = collide_vec<VAR, C::kUnits>(f, p, bad);
         if constexpr (VAR != kLBGK) {
             if (a.fix_list) record_fix_mask<NV>(hits, y * a.nx + x0 + lx, a);
         }
@@ -269,12 +269,12 @@ step_tma(const typename C::S* __restrict__ src, typename C::S* __restrict__ dst,
             if constexpr (std::is_same<C, CodecF16>::value && NV % 2 == 0) {
                 unsigned pk[NV / 2];
 #pragma unroll
-                for (int q = 0; q < NV; q += 2) pk[q / 2] = C::encode2(f[q][i], f[q + 1][i], i, a.cs);
+                for (int q = 0; q < NV; q += 2) pk[q / 2] = C::store2(f[q][i], f[q + 1][i], i, a.cs);
                 Vec<unsigned, NV / 2>::store(reinterpret_cast<unsigned*>(dst + (long long)i * a.plane + o), pk);
             } else {
                 S out[NV];
 #pragma unroll
-                for (int q = 0; q < NV; ++q) out[q] = C::encode(f[q][i], i, a.cs);
+                for (int q = 0; q < NV; ++q) out[q] = C::store(f[q][i], i, a.cs);
                 Vec<S, NV>::store(dst + (long long)i * a.plane + o, out);
             }
         }
