@@ -35,14 +35,13 @@ __host__ __device__ constexpr int wclass(int i)
 }
 
 // Scale of the half-precision encoding (unused by the other codecs): S and,
-// per weight class, the decode factor W/S and the encode factor S/W, each
-// rounded once on the host, so that the kernels take them from the
-// parameter bank instead of forming them per thread.
+// per weight class, the decode factor W/S, rounded once on the host so that
+// the kernels take it from the parameter bank instead of forming it per
+// thread.
 struct CodecScale {
     float scale;      // S
     float inv_scale;  // 1 / S
     float dec[3];     // W_c / S
-    float enc[3];     // S / W_c
 };
 
 __host__ inline CodecScale make_scale(double s)
@@ -51,16 +50,12 @@ __host__ inline CodecScale make_scale(double s)
     CodecScale c;
     c.scale = (float)s;
     c.inv_scale = (float)(1.0 / s);
-    for (int k = 0; k < 3; ++k) {
-        c.dec[k] = (float)(w[k] / s);
-        c.enc[k] = (float)(s / w[k]);
-    }
+    for (int k = 0; k < 3; ++k) c.dec[k] = (float)(w[k] / s);
     return c;
 }
 
 // Storage codecs: S = stored element, T = arithmetic type.
 //   decode(s, i, c)     -> d_i = f_i - W_i in T
-//   encode(d, i, c)     -> stored element
 //   load(s, i, c), store(e, i, c)
 //                       -> the step kernels' view: the value the collision
 //                          works on, d_i itself, or with kUnits the storage
@@ -83,7 +78,6 @@ struct CodecF64 {
     static constexpr int kRowMinBlocks = 1;
     static constexpr bool kUnits = false;
     __device__ __forceinline__ static T decode(S s, int, const CodecScale&) { return s; }
-    __device__ __forceinline__ static S encode(T d, int, const CodecScale&) { return d; }
     __device__ __forceinline__ static T load(S s, int, const CodecScale&) { return s; }
     __device__ __forceinline__ static S store(T d, int, const CodecScale&) { return d; }
     __device__ __forceinline__ static double to_f64(S s, int, const CodecScale&) { return s; }
@@ -97,7 +91,6 @@ struct CodecF32 {
     static constexpr int kRowMinBlocks = 12;
     static constexpr bool kUnits = false;
     __device__ __forceinline__ static T decode(S s, int, const CodecScale&) { return s; }
-    __device__ __forceinline__ static S encode(T d, int, const CodecScale&) { return d; }
     __device__ __forceinline__ static T load(S s, int, const CodecScale&) { return s; }
     __device__ __forceinline__ static S store(T d, int, const CodecScale&) { return d; }
     __device__ __forceinline__ static double to_f64(S s, int, const CodecScale&) { return (double)s; }
@@ -130,10 +123,6 @@ struct CodecF16 {
     __device__ __forceinline__ static T decode(S s, int i, const CodecScale& c)
     {
         return __half2float(__ushort_as_half(s)) * c.dec[wclass(i)];
-    }
-    __device__ __forceinline__ static S encode(T d, int i, const CodecScale& c)
-    {
-        return __half_as_ushort(__float2half_rn(d * c.enc[wclass(i)]));
     }
     __device__ __forceinline__ static double to_f64(S s, int i, const CodecScale& c)
     {

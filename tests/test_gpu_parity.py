@@ -600,3 +600,37 @@ def test_guard_count_and_full_fp64_pass():
     lat.close()
     ref = representable(O.step(g, O.B, beta, 1), "f32")
     assert np.max(np.abs(got - ref)) <= 2 * np.finfo(np.float32).eps * 0.05
+
+
+@pytest.mark.parametrize("kernel", ["rows", "bulk", "nodes"])
+def test_f16_guard_threshold_in_storage_units(kernel):
+    """FP16 steps collide in the storage units, where the guard compares
+    <dh|dh> scaled by (36 S)^2 against the threshold scaled alike.  With the
+    threshold at the median of rho <dh|dh> over the nodes (from the oracle's
+    split of the pulled F16 field), the guard count lies between the nodes
+    below half and below twice the threshold; the FP64-recomputed result
+    stays within the F16 tolerance of the oracle step."""
+    nx, ny, beta, scale = 512, 8, 0.97, 4.0
+    g = representable(random_field(nx, ny, 91, amp=0.02), "f16", f16_scale=scale)
+    f = np.empty_like(g)
+    for i in range(9):
+        a, b = i % 3 - 1, i // 3 - 1
+        f[i] = np.roll(g[i], shift=(b, a), axis=(0, 1))
+    nodes = f.reshape(9, -1).T
+    sp = O.split(O.B, nodes)
+    hh = nodes.sum(1) * np.sum(sp["dh"] ** 2 / sp["feq"], axis=1)
+    tau = float(np.median(hh))
+    lo, hi = int(np.sum(hh < 0.5 * tau)), int(np.sum(hh <= 2.0 * tau))
+    lat = Lattice(nx, ny, variant="B", beta=beta, dtype="f16")
+    lat.set_f16_scale(scale)
+    lat.set_kernel(kernel)
+    lat.set_guard(tau)
+    lat.set_populations(g)
+    lat.step(1)
+    count = lat.guard_count()
+    got = lat.populations().cpu().numpy()
+    lat.close()
+    assert lo <= count <= hi, (lo, count, hi)
+    ref = O.step(g, O.B, beta, 1)
+    W = O.weights()[:, None, None]
+    assert np.max(np.abs(got - ref) / W) <= 2e-3
