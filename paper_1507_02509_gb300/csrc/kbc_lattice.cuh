@@ -65,9 +65,9 @@ __host__ inline CodecScale make_scale(double s)
 // kVec: nodes per thread of the vector-row kernel (kVec * sizeof(S) bytes
 // per load/store; 16 for F64/F32, 8 for F16, which keeps F16 registers low).
 // kRowMinBlocks: resident 64-thread blocks per SM the vector-row kernel is
-// compiled for.  12 caps it at 80 registers (65536 / (12 * 64) = 85; KBC A/B
-// spill 20 bytes, which costs nothing measurable) and keeps 24 warps per SM
-// loading: 3% faster than 96 registers for KBC B and 5% for C/D.  Left free,
+// compiled for.  12 caps it at 80 registers (65536 / (12 * 64) = 85; every
+// variant fits without spilling) and keeps 24 warps per SM loading: 3%
+// faster than 96 registers for KBC B and 5% for C/D.  Left free,
 // the compiler takes up to 190 registers and the bandwidth-bound FP32 step
 // loses a third of its rate.  FP64 is bound by its arithmetic pipe, not by
 // occupancy.
