@@ -160,8 +160,10 @@ int kbc_set_guard(kbc_handle h, double threshold);
  * (synchronises the stream; 0 when the pass is off). */
 int kbc_guard_count(kbc_handle h, long long* count);
 
-/* Scale S of the F16 encoding (f - W)/W * S; must be set before kbc_init.
- * Default 1. */
+/* Scale S of the F16 encoding (f - W)/W * S; must be set before kbc_init
+ * (else KBC_ERR_STATE).  Default 1; S outside [2^-24, 2^24] (where the half
+ * code or the float constants derived from S would over- or underflow) is
+ * rejected with KBC_ERR_ARG. */
 int kbc_set_f16_scale(kbc_handle h, double scale);
 
 /* Initialise the field to the equilibrium f^eq(rho, u) of Eq. Eq at every

@@ -758,7 +758,8 @@ int kbc_guard_count(kbc_handle h, long long* count)
 int kbc_set_f16_scale(kbc_handle h, double scale)
 {
     if (!h) return KBC_ERR_ARG;
-    if (!(scale > 0.0 && std::isfinite(scale))) return fail(h, KBC_ERR_ARG, "scale must be > 0");
+    if (!(scale >= 0x1p-24 && scale <= 0x1p24))
+        return fail(h, KBC_ERR_ARG, "scale must lie in [2^-24, 2^24]");
     if (h->initialized) return fail(h, KBC_ERR_STATE, "set the scale before kbc_init");
     h->f16_scale = (float)scale;
     ++h->config_version;

@@ -573,6 +573,10 @@ def test_f16_scale(scale):
     nx, ny = 256, 5
     g = representable(random_field(nx, ny, 61), "f16", f16_scale=scale)
     lat = Lattice(nx, ny, variant="B", beta=0.97, dtype="f16")
+    for bad in (0.0, -1.0, 1e30, 1e-30, math.inf, math.nan):
+        with pytest.raises(KBCError) as e:
+            lat.set_f16_scale(bad)
+        assert e.value.status == capi.KBC_ERR_ARG
     lat.set_f16_scale(scale)
     lat.set_populations(g)
     lat.step(1)
