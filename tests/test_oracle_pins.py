@@ -432,6 +432,34 @@ def test_rotation_equivariance(variant):
     assert np.allclose(a, b, rtol=0, atol=1e-14)
 
 
+def _mirror_x_field(g):
+    """Reflect the lattice in x: node (x, y) -> (-x, y) and velocity
+    (a, b) -> (-a, b)."""
+    out = np.empty_like(g)
+    for i in range(9):
+        a, b = int(O.VA[i]), int(O.VB[i])
+        j = 3 * (b + 1) + (-a + 1)  # index of (-a, b)
+        out[j] = np.roll(g[i][:, ::-1], 1, axis=1)  # column x -> (-x) mod n
+    return out
+
+
+@pytest.mark.parametrize("variant", (O.LBGK,) + KBC)
+def test_mirror_equivariance(variant):
+    """The D2Q9 velocity set, the weights, the equilibrium and each variant's
+    split are symmetric under x -> -x, so stepping commutes with the
+    reflection (a handedness slip, which a 90 degree rotation can map onto
+    itself, would not)."""
+    rng = np.random.default_rng(19)
+    n = 8
+    g = O.init_feq(1 + 0.01 * rng.standard_normal((n, n)), 0.05 * rng.standard_normal((n, n)),
+                   0.05 * rng.standard_normal((n, n)))
+    g = O.step(g, variant, 0.9, 2)
+    a = _mirror_x_field(O.step(g, variant, 0.9, 3))
+    b = O.step(_mirror_x_field(g), variant, 0.9, 3)
+    assert np.allclose(a, b, rtol=0, atol=1e-14)
+    assert not np.allclose(g, _mirror_x_field(g), rtol=0, atol=1e-6)  # the field is not symmetric
+
+
 def _tg_rate(variant, n, u0, nu, steps):
     from paper_1507_02509_gb300 import flows
 
