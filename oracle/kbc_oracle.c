@@ -295,6 +295,19 @@ void kbco_macro(int nx, int ny, const double* g, double* rho, double* ux,
     }
 }
 
+/* Mean and standard deviation of n values by the plain two-pass definition:
+ * the mean first, then the mean of the squared deviations from it. */
+static void mean_std(const double* v, size_t n, double* mean, double* std)
+{
+    double m = 0.0;
+    for (size_t c = 0; c < n; ++c) m += v[c];
+    m /= (double)n;
+    double q = 0.0;
+    for (size_t c = 0; c < n; ++c) q += (v[c] - m) * (v[c] - m);
+    *mean = m;
+    *std = sqrt(q / (double)n);
+}
+
 /*
  * Global diagnostics of the field (the quantities plotted in the paper's
  * shear-layer and turbulence sections), in this order:
@@ -313,9 +326,14 @@ int kbco_diagnostics(int nx, int ny, int variant, double beta, int gmode,
     double* rho = malloc(np * sizeof(double));
     double* ux = malloc(np * sizeof(double));
     double* uy = malloc(np * sizeof(double));
-    if (!rho || !ux || !uy) { free(rho); free(ux); free(uy); return -2; }
+    double* ke = malloc(np * sizeof(double));
+    double* zz = malloc(np * sizeof(double));
+    if (!rho || !ux || !uy || !ke || !zz) {
+        free(rho); free(ux); free(uy); free(ke); free(zz);
+        return -2;
+    }
     kbco_macro(nx, ny, g, rho, ux, uy);
-    double mass = 0, px = 0, py = 0, e = 0, e2 = 0, z = 0, z2 = 0;
+    double mass = 0, px = 0, py = 0;
     double gsum = 0, gmin = INFINITY, gmax = -INFINITY;
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
@@ -323,12 +341,10 @@ int kbco_diagnostics(int nx, int ny, int variant, double beta, int gmode,
             mass += rho[c];
             px += rho[c] * ux[c];
             py += rho[c] * uy[c];
-            const double ke = 0.5 * (ux[c] * ux[c] + uy[c] * uy[c]);
-            e += ke; e2 += ke * ke;
+            ke[c] = 0.5 * (ux[c] * ux[c] + uy[c] * uy[c]);
             const double w = 0.5 * (uy[(size_t)y * nx + wrap(x + 1, nx)] - uy[(size_t)y * nx + wrap(x - 1, nx)])
                            - 0.5 * (ux[wrap(y + 1, ny) * nx + x] - ux[wrap(y - 1, ny) * nx + x]);
-            const double zz = 0.5 * w * w;
-            z += zz; z2 += zz * zz;
+            zz[c] = 0.5 * w * w;
             double f[9], o[9], gm;
             pull(nx, ny, g, x, y, f);
             collide_r(variant, beta, gmode, gfix, 0, f, o, &gm);
@@ -336,13 +352,11 @@ int kbco_diagnostics(int nx, int ny, int variant, double beta, int gmode,
             if (gm < gmin) gmin = gm;
             if (gm > gmax) gmax = gm;
         }
-    const double inv = 1.0 / (double)np;
     out[0] = mass; out[1] = px; out[2] = py;
-    out[3] = e * inv; out[4] = z * inv;
-    out[5] = gsum * inv; out[6] = gmin; out[7] = gmax;
-    out[8] = sqrt(fmax(e2 * inv - (e * inv) * (e * inv), 0.0));
-    out[9] = sqrt(fmax(z2 * inv - (z * inv) * (z * inv), 0.0));
-    free(rho); free(ux); free(uy);
+    mean_std(ke, np, &out[3], &out[8]);
+    mean_std(zz, np, &out[4], &out[9]);
+    out[5] = gsum / (double)np; out[6] = gmin; out[7] = gmax;
+    free(rho); free(ux); free(uy); free(ke); free(zz);
     return 0;
 }
 
@@ -362,34 +376,34 @@ int kbco_diagnostics_ext(int nx, int ny, const double* g, double* out)
     double* ux = malloc(np * sizeof(double));
     double* uy = malloc(np * sizeof(double));
     double* w = malloc(np * sizeof(double));
-    if (!rho || !ux || !uy || !w) { free(rho); free(ux); free(uy); free(w); return -2; }
+    double* pd = malloc(np * sizeof(double));
+    double* sd = malloc(np * sizeof(double));
+    if (!rho || !ux || !uy || !w || !pd || !sd) {
+        free(rho); free(ux); free(uy); free(w); free(pd); free(sd);
+        return -2;
+    }
     kbco_macro(nx, ny, g, rho, ux, uy);
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x)
             w[(size_t)y * nx + x] =
                 0.5 * (uy[(size_t)y * nx + wrap(x + 1, nx)] - uy[(size_t)y * nx + wrap(x - 1, nx)])
               - 0.5 * (ux[wrap(y + 1, ny) * nx + x] - ux[wrap(y - 1, ny) * nx + x]);
-    double p = 0, p2 = 0, e = 0, e2 = 0;
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             const size_t c = (size_t)y * nx + x;
             const double wx = 0.5 * (w[(size_t)y * nx + wrap(x + 1, nx)] - w[(size_t)y * nx + wrap(x - 1, nx)]);
             const double wy = 0.5 * (w[wrap(y + 1, ny) * nx + x] - w[wrap(y - 1, ny) * nx + x]);
-            const double pp = 0.5 * (wx * wx + wy * wy);
-            p += pp; p2 += pp * pp;
+            pd[c] = 0.5 * (wx * wx + wy * wy);
             double s = 0.0;
             for (int i = 0; i < 9; ++i) {
                 const double f = g[i * np + c];
                 s -= f * log(f / kbco_W(i));
             }
-            e += s; e2 += s * s;
+            sd[c] = s;
         }
-    const double inv = 1.0 / (double)np;
-    out[0] = p * inv;
-    out[1] = sqrt(fmax(p2 * inv - (p * inv) * (p * inv), 0.0));
-    out[2] = e * inv;
-    out[3] = sqrt(fmax(e2 * inv - (e * inv) * (e * inv), 0.0));
-    free(rho); free(ux); free(uy); free(w);
+    mean_std(pd, np, &out[0], &out[1]);
+    mean_std(sd, np, &out[2], &out[3]);
+    free(rho); free(ux); free(uy); free(w); free(pd); free(sd);
     return 0;
 }
 

@@ -545,13 +545,18 @@ def test_grad_initialisation_moments():
     assert np.allclose(mom(gn, 1, 1), rho * ux * uy - c * dxy, atol=1e-16)
 
 
-def test_diagnostics_taylor_green_closed_forms():
-    """For the discrete vortex at equilibrium: E = u0^2/4 and, with central
-    differences, Z = u0^2 sin(k)^2 / 2; the momentum sums vanish; LBGK reports
-    gamma = 2 everywhere."""
+@pytest.mark.parametrize("n", [8, 12, 32])
+def test_diagnostics_taylor_green_closed_forms(n):
+    """For the discrete vortex at equilibrium, with C, S = cos, sin(kx) and
+    c, s = cos, sin(ky): |u|^2/2 = (u0^2/2)(C^2 s^2 + S^2 c^2) and, with
+    central differences, w = 2 u0 sin(k) C c.  Grid means of cos^2, cos^4 and
+    cos^2 sin^2 are 1/2, 3/8 and 1/8 (n > 4), so E = u0^2/4 with spatial std
+    u0^2/8, and Z = u0^2 sin(k)^2/2 with std (sqrt(5)/4) u0^2 sin(k)^2 (the
+    RMS histories of the shear-layer and turbulence sections).  The momentum
+    sums vanish; LBGK reports gamma = 2 everywhere."""
     from paper_1507_02509_gb300 import flows
 
-    n, u0 = 32, 0.03
+    u0 = 0.03
     rho, ux, uy = flows.taylor_green(n, u0=u0)
     g = O.init_feq(rho, ux, uy)
     d = O.diagnostics(g, O.B, 0.9)
@@ -560,9 +565,29 @@ def test_diagnostics_taylor_green_closed_forms():
     assert abs(d[1]) < 1e-13 and abs(d[2]) < 1e-13
     assert d[3] == pytest.approx(u0 * u0 / 4, rel=1e-13)
     assert d[4] == pytest.approx(0.5 * u0 * u0 * math.sin(k) ** 2, rel=1e-12)
+    assert d[8] == pytest.approx(u0 * u0 / 8, rel=1e-13)
+    assert d[9] == pytest.approx(math.sqrt(5) / 4 * u0 * u0 * math.sin(k) ** 2, rel=1e-12)
     assert d[6] <= d[5] <= d[7]
     dl = O.diagnostics(g, O.LBGK, 0.9)
     assert dl[5] == dl[6] == dl[7] == 2.0
+
+
+def test_diagnostics_std_of_two_valued_fields():
+    """A field whose nodes take one of two values with equal frequency has
+    spatial std |v1 - v2| / 2: uniform flows (U1, 0) and (U2, 0) on
+    alternating pairs of rows for |u|^2/2; every row then has one neighbour
+    row of each kind, so central differences give w = +-(U1 - U2)/2 and
+    w^2/2 is uniform (std 0)."""
+    nx, ny, U1, U2 = 6, 8, 0.05, -0.02
+    ux = np.full((ny, nx), U1)
+    ux[2::4, :] = U2
+    ux[3::4, :] = U2
+    rho, uy = np.ones((ny, nx)), np.zeros((ny, nx))
+    d = O.diagnostics(O.init_feq(rho, ux, uy), O.LBGK, 0.9)
+    assert d[3] == pytest.approx(0.25 * (U1 * U1 + U2 * U2), rel=1e-14)
+    assert d[8] == pytest.approx(0.25 * abs(U1 * U1 - U2 * U2), rel=1e-13)
+    assert d[4] == pytest.approx(0.5 * (0.5 * (U1 - U2)) ** 2, rel=1e-14)
+    assert d[9] < 1e-15 * d[4]
 
 
 # ---------------------------------------------------------------- adjoint oracle
@@ -670,8 +695,9 @@ def test_exact_gamma_limits():
 
 def test_diagnostics_ext_closed_forms():
     """Palinstrophy of the discrete vortex with central differences is
-    u0^2 sin(k)^4; the entropy density of Eq. S vanishes at rest with unit
-    density and is -rho ln rho for a uniform density at rest."""
+    u0^2 sin(k)^4 with spatial std u0^2 sin(k)^4 / 2; the entropy density of
+    Eq. S vanishes at rest with unit density and is -rho ln rho for a density
+    at rest, so a two-valued density gives the mean and std of two values."""
     from paper_1507_02509_gb300 import flows
 
     n, u0 = 32, 0.03
@@ -679,13 +705,22 @@ def test_diagnostics_ext_closed_forms():
     k = 2 * math.pi / n
     d = O.diagnostics_ext(O.init_feq(rho, ux, uy))
     assert d[0] == pytest.approx(u0 * u0 * math.sin(k) ** 4, rel=1e-11)
+    # |grad w|^2/2 = 2 u0^2 sin(k)^4 (S^2 c^2 + C^2 s^2): std u0^2 sin(k)^4 / 2
+    assert d[1] == pytest.approx(0.5 * u0 * u0 * math.sin(k) ** 4, rel=1e-11)
     rest = O.init_feq(np.ones((4, 6)), np.zeros((4, 6)), np.zeros((4, 6)))
     d = O.diagnostics_ext(rest)
-    assert abs(d[2]) < 1e-16 and d[0] == 0.0
+    assert abs(d[2]) < 1e-16 and d[0] == 0.0 and d[1] == 0.0
     r0 = 1.3
     d = O.diagnostics_ext(O.init_feq(np.full((4, 6), r0), np.zeros((4, 6)), np.zeros((4, 6))))
     assert d[2] == pytest.approx(-r0 * math.log(r0), rel=1e-14)
-    assert d[3] < 3e-8  # one-pass variance: resolution sqrt(eps) |mean|
+    assert d[3] <= 1e-15 * abs(d[2])  # identical values: std at the rounding of the mean
+    # two densities on alternate rows at rest: s = -rho ln rho takes two values
+    r = np.full((4, 6), r0)
+    r[1::2, :] = 0.7
+    d = O.diagnostics_ext(O.init_feq(r, np.zeros((4, 6)), np.zeros((4, 6))))
+    s1, s2 = -r0 * math.log(r0), -0.7 * math.log(0.7)
+    assert d[2] == pytest.approx(0.5 * (s1 + s2), rel=1e-14)
+    assert d[3] == pytest.approx(0.5 * abs(s1 - s2), rel=1e-13)
 
 
 def test_spectra_oracle_parseval_and_single_mode():
