@@ -252,8 +252,9 @@ int kbc_spectrum(int n, const double* u, int nbins, double* E, double* Z, void* 
  * arena sized at start-up), and code that must not trigger the implicit
  * device-wide synchronisation of cudaMalloc/cudaFree inside a timed loop.
  * It needs no handle: f is the caller's FP64 population field
- * f[9][ny][nx] in DEVICE memory (a host pointer gives KBC_ERR_ARG, since
- * staging it would need an allocation); out (host or device) receives the
+ * f[9][ny][nx] in DEVICE memory of the current device (a host pointer
+ * gives KBC_ERR_ARG, since staging it would need an allocation, and so does
+ * a field on another device); out (host or device) receives the
  * KBC_DIAG_N values documented at kbc_diagnostics, for the given variant
  * and beta with the entropic gamma.  Work runs on `stream` (a cudaStream_t,
  * NULL = legacy default) and the call waits for it (bounded,
@@ -263,8 +264,10 @@ int kbc_spectrum(int n, const double* u, int nbins, double* E, double* Z, void* 
  * loads the library holds until the process exits; it bounds the grid to
  * nx * ny <= 2^28 nodes (e.g. 16384 x 16384); larger grids give
  * KBC_ERR_ARG.  The first call on each device looks up the array's device
- * address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.  All calls share the array, so calls that
+ * address (cudaGetSymbolAddress) with that device current, and caches it
+ * for that device's context (a call after cudaDeviceReset, which ends the
+ * context, looks it up again); make that first call before any stream
+ * capture.  All calls share the array, so calls that
  * overlap on the GPU (different streams or threads) race and must be
  * serialised by the caller.  Nothing in the array needs clearing: every
  * call overwrites the parts it reads. */

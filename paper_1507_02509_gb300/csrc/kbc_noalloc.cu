@@ -6,10 +6,14 @@
 // device array.  Host code must not hand the array's name to a kernel: on
 // the host that name is only a stand-in, and on a GPU that can reach host
 // memory the kernel would silently work on the wrong memory.  The device
-// address is fetched once per device with cudaGetSymbolAddress and cached.
+// address is fetched with cudaGetSymbolAddress once per device and context
+// (the context's unique id tells a context created after cudaDeviceReset
+// from the one the cached address belongs to) and cached.
 #include <chrono>
 #include <mutex>
 #include <thread>
+
+#include <cudaTypedefs.h>
 
 #include "../../include/kbc.h"
 #include "kbc_launch.cuh"
@@ -35,6 +39,28 @@ __device__ __align__(256) double g_noalloc_scratch[kMaxBlocks * kDiagParts + 32]
 
 std::mutex g_mu;
 double* g_scratch_addr[kMaxDevices] = {};
+unsigned long long g_scratch_ctx[kMaxDevices] = {};
+
+// Unique id of the current context (0 when it cannot be had: the address is
+// then looked up on every call instead of cached).
+unsigned long long current_context_id()
+{
+    static PFN_cuCtxGetId_v12000 get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<PFN_cuCtxGetId_v12000>(fn);
+        cudaGetLastError();
+        looked_up = true;
+    }
+    unsigned long long id = 0;
+    if (!get_id || get_id(nullptr, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
 
 }  // namespace
 }  // namespace kbc
@@ -58,16 +84,20 @@ extern "C" int kbc_diagnostics_noalloc(int nx, int ny, int variant, double beta,
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return KBC_ERR_CUDA;
+    // the kernels read f directly: it must live on the current device
+    if (at.type == cudaMemoryTypeDevice && at.device != dev) return KBC_ERR_ARG;
     double* scratch = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_mu);
-        if (!g_scratch_addr[dev]) {
+        const unsigned long long ctx = current_context_id();
+        if (!g_scratch_addr[dev] || ctx == 0 || g_scratch_ctx[dev] != ctx) {
             void* p = nullptr;
             if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
                 cudaGetLastError();
                 return KBC_ERR_CUDA;
             }
             g_scratch_addr[dev] = static_cast<double*>(p);
+            g_scratch_ctx[dev] = ctx;
         }
         scratch = g_scratch_addr[dev];
     }
