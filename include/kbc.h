@@ -260,7 +260,7 @@ int kbc_spectrum(int n, const double* u, int nbins, double* E, double* Z, void* 
  * NULL = legacy default) and the call waits for it (bounded,
  * KBC_ERR_TIMEOUT).
  *
- * Scratch: a file-scope device array of about 1.3 MB that every GPU that
+ * Scratch: a file-scope device array of about 1.4 MB that every GPU that
  * loads the library holds until the process exits; it bounds the grid to
  * nx * ny <= 2^28 nodes (e.g. 16384 x 16384); larger grids give
  * KBC_ERR_ARG.  The first call on each device looks up the array's device

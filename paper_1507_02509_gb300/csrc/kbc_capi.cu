@@ -21,40 +21,30 @@ namespace kbc {
 __global__ void diag_final(const double* __restrict__ part, int nblocks, double* __restrict__ out,
                            long long total)
 {
-    // one block; thread t sums blocks t, t + blockDim, ... in a fixed order
+    // one block; thread t folds blocks t, t + blockDim, ... in a fixed order,
+    // then a fixed tree combines the threads
     __shared__ double sm[kDiagParts][kDiagBlock];
-    double acc[kDiagParts] = {0, 0, 0, 0, 0, 0, 0, 0, 1e300, -1e300};
-    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
-#pragma unroll
-        for (int k = 0; k < 8; ++k) acc[k] += part[(long long)b * kDiagParts + k];
-        acc[8] = fmin(acc[8], part[(long long)b * kDiagParts + 8]);
-        acc[9] = fmax(acc[9], part[(long long)b * kDiagParts + 9]);
-    }
+    double acc[kDiagParts] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 1e300, -1e300};
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+        diag_fold(acc, 1, part + (long long)b * kDiagParts, 1);
 #pragma unroll
     for (int k = 0; k < kDiagParts; ++k) sm[k][threadIdx.x] = acc[k];
     __syncthreads();
     for (int s = kDiagBlock / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) {
-#pragma unroll
-            for (int k = 0; k < 8; ++k) sm[k][threadIdx.x] += sm[k][threadIdx.x + s];
-            sm[8][threadIdx.x] = fmin(sm[8][threadIdx.x], sm[8][threadIdx.x + s]);
-            sm[9][threadIdx.x] = fmax(sm[9][threadIdx.x], sm[9][threadIdx.x + s]);
-        }
+        if (threadIdx.x < s) diag_fold(&sm[0][threadIdx.x], kDiagBlock, &sm[0][threadIdx.x + s], kDiagBlock);
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        const double inv = 1.0 / (double)total;
-        const double e = sm[3][0] * inv, z = sm[5][0] * inv;
         out[0] = sm[0][0];
         out[1] = sm[1][0];
         out[2] = sm[2][0];
-        out[3] = e;
-        out[4] = z;
-        out[5] = sm[7][0] * inv;
-        out[6] = sm[8][0];
-        out[7] = sm[9][0];
-        out[8] = sqrt(fmax(sm[4][0] * inv - e * e, 0.0));
-        out[9] = sqrt(fmax(sm[6][0] * inv - z * z, 0.0));
+        out[3] = sm[4][0];
+        out[4] = sm[6][0];
+        out[5] = sm[8][0] / (double)total;
+        out[6] = sm[9][0];
+        out[7] = sm[10][0];
+        out[8] = sqrt(fmax(sm[5][0], 0.0) / (double)total);
+        out[9] = sqrt(fmax(sm[7][0], 0.0) / (double)total);
     }
 }
 
@@ -62,28 +52,22 @@ __global__ void diag_ext_final(const double* __restrict__ part, int nblocks, dou
                                long long total)
 {
     __shared__ double sm[kDiagExtParts][kDiagBlock];
-    double acc[kDiagExtParts] = {0, 0, 0, 0};
-    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
-#pragma unroll
-        for (int k = 0; k < kDiagExtParts; ++k) acc[k] += part[(long long)b * kDiagExtParts + k];
-    }
+    double acc[kDiagExtParts] = {0, 0, 0, 0, 0};
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+        diag_ext_fold(acc, 1, part + (long long)b * kDiagExtParts, 1);
 #pragma unroll
     for (int k = 0; k < kDiagExtParts; ++k) sm[k][threadIdx.x] = acc[k];
     __syncthreads();
     for (int s = kDiagBlock / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) {
-#pragma unroll
-            for (int k = 0; k < kDiagExtParts; ++k) sm[k][threadIdx.x] += sm[k][threadIdx.x + s];
-        }
+        if (threadIdx.x < s)
+            diag_ext_fold(&sm[0][threadIdx.x], kDiagBlock, &sm[0][threadIdx.x + s], kDiagBlock);
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        const double inv = 1.0 / (double)total;
-        const double p = sm[0][0] * inv, e = sm[2][0] * inv;
-        out[0] = p;
-        out[1] = sqrt(fmax(sm[1][0] * inv - p * p, 0.0));
-        out[2] = e;
-        out[3] = sqrt(fmax(sm[3][0] * inv - e * e, 0.0));
+        out[0] = sm[1][0];
+        out[1] = sqrt(fmax(sm[2][0], 0.0) / (double)total);
+        out[2] = sm[3][0];
+        out[3] = sqrt(fmax(sm[4][0], 0.0) / (double)total);
     }
 }
 

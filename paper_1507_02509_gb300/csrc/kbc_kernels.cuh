@@ -469,13 +469,42 @@ __global__ void moments(const typename C::S* __restrict__ src, double* __restric
 
 // ---------------------------------------------------------------- diagnostics
 //
-// Per block: FP64 partial sums of mass, momentum, |u|^2/2 and its square,
-// w^2/2 and its square, gamma (sum, min, max) over a grid-stride range of
-// nodes, written to part[block][10].  gamma is that of the collision the next
-// step performs, evaluated in double.  Deterministic: fixed grid, fixed
-// reduction order.
-constexpr int kDiagParts = 10;
+// Per block: FP64 partial sums of mass and momentum, the count, mean and sum
+// of squared deviations (M2) of |u|^2/2 and of w^2/2, and gamma (sum, min,
+// max) over a grid-stride range of nodes, written to part[block][11].  gamma
+// is that of the collision the next step performs, evaluated in double.
+// Means and M2 are accumulated per thread by Welford's update and combined
+// across threads and blocks by Chan et al.'s pairwise formula, so the
+// standard deviations need no E[x^2] - E[x]^2 difference (which cancels).
+// Deterministic: fixed grid, fixed reduction order.
+constexpr int kDiagParts = 11;
 constexpr int kDiagBlock = 256;
+
+// Welford's running update of (count n, mean m, M2 q) with one value x.
+__device__ __forceinline__ void welford_add(double& n, double& m, double& q, double x)
+{
+    n += 1.0;
+    const double d = x - m;
+    m += d / n;
+    q += d * (x - m);
+}
+
+// Chan, Golub and LeVeque's combination of two partial (n, m, q) sets: the
+// second is folded into the first.  mb and qb belong to the same nb.
+__device__ __forceinline__ void chan_merge(double na, double nb, double& ma, double& qa, double mb,
+                                           double qb)
+{
+    const double n = na + nb;
+    if (nb == 0.0) return;
+    if (na == 0.0) {
+        ma = mb;
+        qa = qb;
+        return;
+    }
+    const double d = mb - ma;
+    ma += d * (nb / n);
+    qa += qb + d * d * (na * nb / n);
+}
 
 // Tiles of the diagnostics kernels: kTileW x kTileH nodes per block
 // iteration (two per thread), with rho and u computed once per position of
@@ -489,13 +518,30 @@ __device__ __forceinline__ int wrap_mod(int v, int n)
     return v < 0 ? v + n : v;
 }
 
+// Folds partial set b into partial set a of the diagnostics; element k of a
+// set is at a[k * sa] (b[k * sb]).
+__device__ __forceinline__ void diag_fold(double* a, int sa, const double* b, int sb)
+{
+    a[0] += b[0];
+    a[sa] += b[sb];
+    a[2 * sa] += b[2 * sb];
+    const double na = a[3 * sa], nb = b[3 * sb];
+    chan_merge(na, nb, a[4 * sa], a[5 * sa], b[4 * sb], b[5 * sb]);
+    chan_merge(na, nb, a[6 * sa], a[7 * sa], b[6 * sb], b[7 * sb]);
+    a[3 * sa] = na + nb;
+    a[8 * sa] += b[8 * sb];
+    a[9 * sa] = fmin(a[9 * sa], b[9 * sb]);
+    a[10 * sa] = fmax(a[10 * sa], b[10 * sb]);
+}
+
 template <int VAR, class C>
 __global__ void __launch_bounds__(kDiagBlock)
 diag_partial(const typename C::S* __restrict__ src, double* __restrict__ part, StepArgs a)
 {
     constexpr int HW = kTileW + 2, HH = kTileH + 2;  // one-node halo
     __shared__ double sr[HH][HW], sux[HH][HW], suy[HH][HW];
-    double acc[kDiagParts] = {0, 0, 0, 0, 0, 0, 0, 0, 1e300, -1e300};
+    // mass, px, py, n, mean and M2 of |u|^2/2, of w^2/2, gamma sum, min, max
+    double acc[kDiagParts] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 1e300, -1e300};
     CollideParams<double> p = a.pd;
     p.guard = 0.0;
     const int ntx = (a.nx + kTileW - 1) / kTileW, nty = (a.ny + kTileH - 1) / kTileH;
@@ -519,12 +565,11 @@ diag_partial(const typename C::S* __restrict__ src, double* __restrict__ part, S
             acc[1] += r * ux;
             acc[2] += r * uy;
             const double ke = 0.5 * (ux * ux + uy * uy);
-            acc[3] += ke;
-            acc[4] += ke * ke;
             const double w = 0.5 * (suy[cy][cx + 1] - suy[cy][cx - 1]) - 0.5 * (sux[cy + 1][cx] - sux[cy - 1][cx]);
             const double zz = 0.5 * w * w;
-            acc[5] += zz;
-            acc[6] += zz * zz;
+            double cnt = acc[3];
+            welford_add(cnt, acc[4], acc[5], ke);
+            welford_add(acc[3], acc[6], acc[7], zz);
             double f[9];
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
@@ -537,9 +582,9 @@ diag_partial(const typename C::S* __restrict__ src, double* __restrict__ part, S
             double rr;
             bool hit;
             const double g = collide_node<VAR>(f, p, rr, hit);
-            acc[7] += g;
-            acc[8] = fmin(acc[8], g);
-            acc[9] = fmax(acc[9], g);
+            acc[8] += g;
+            acc[9] = fmin(acc[9], g);
+            acc[10] = fmax(acc[10], g);
         }
     }
     __shared__ double sm[kDiagParts][kDiagBlock];
@@ -547,12 +592,7 @@ diag_partial(const typename C::S* __restrict__ src, double* __restrict__ part, S
     for (int k = 0; k < kDiagParts; ++k) sm[k][threadIdx.x] = acc[k];
     __syncthreads();
     for (int s = kDiagBlock / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) {
-#pragma unroll
-            for (int k = 0; k < 8; ++k) sm[k][threadIdx.x] += sm[k][threadIdx.x + s];
-            sm[8][threadIdx.x] = fmin(sm[8][threadIdx.x], sm[8][threadIdx.x + s]);
-            sm[9][threadIdx.x] = fmax(sm[9][threadIdx.x], sm[9][threadIdx.x + s]);
-        }
+        if (threadIdx.x < s) diag_fold(&sm[0][threadIdx.x], kDiagBlock, &sm[0][threadIdx.x + s], kDiagBlock);
         __syncthreads();
     }
     if (threadIdx.x == 0) {
@@ -561,11 +601,20 @@ diag_partial(const typename C::S* __restrict__ src, double* __restrict__ part, S
     }
 }
 
-// Palinstrophy and entropy density per block: part[block][4] = sums of
-// P = |grad w|^2 / 2 (w and its gradient by periodic central differences,
-// the same w as diag_partial), P^2, the entropy density of Eq. S,
-// s = -sum_i f_i ln(f_i / W_i) = -sum_i f_i log1p(d_i / W_i), and s^2.
-constexpr int kDiagExtParts = 4;
+// Palinstrophy and entropy density per block: part[block][5] = count, and
+// the mean and M2 (Welford / Chan, as in diag_partial) of P = |grad w|^2 / 2
+// (w and its gradient by periodic central differences, the same w as
+// diag_partial) and of the entropy density of Eq. S,
+// s = -sum_i f_i ln(f_i / W_i) = -sum_i f_i log1p(d_i / W_i).
+constexpr int kDiagExtParts = 5;
+
+__device__ __forceinline__ void diag_ext_fold(double* a, int sa, const double* b, int sb)
+{
+    const double na = a[0], nb = b[0];
+    chan_merge(na, nb, a[sa], a[2 * sa], b[sb], b[2 * sb]);
+    chan_merge(na, nb, a[3 * sa], a[4 * sa], b[3 * sb], b[4 * sb]);
+    a[0] = na + nb;
+}
 
 template <class C>
 __global__ void __launch_bounds__(kDiagBlock)
@@ -574,7 +623,7 @@ diag_ext_partial(const typename C::S* __restrict__ src, double* __restrict__ par
     // u on the tile with a two-node halo, w on the tile with a one-node halo
     constexpr int UW = kTileW + 4, UH = kTileH + 4, WW = kTileW + 2, WH = kTileH + 2;
     __shared__ double sux[UH][UW], suy[UH][UW], sw[WH][WW];
-    double acc[kDiagExtParts] = {0, 0, 0, 0};
+    double acc[kDiagExtParts] = {0, 0, 0, 0, 0};  // n, mean and M2 of P, of s
     const int ntx = (a.nx + kTileW - 1) / kTileW, nty = (a.ny + kTileH - 1) / kTileH;
     const long long ntiles = (long long)ntx * nty;
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -601,8 +650,6 @@ diag_ext_partial(const typename C::S* __restrict__ src, double* __restrict__ par
             const double wx = 0.5 * (sw[cy][cx + 1] - sw[cy][cx - 1]);
             const double wy = 0.5 * (sw[cy + 1][cx] - sw[cy - 1][cx]);
             const double pp = 0.5 * (wx * wx + wy * wy);
-            acc[0] += pp;
-            acc[1] += pp * pp;
             const long long n = (long long)y * a.nx + x;
             double se = 0.0;
 #pragma unroll
@@ -610,8 +657,9 @@ diag_ext_partial(const typename C::S* __restrict__ src, double* __restrict__ par
                 const double d = C::to_f64(src[(long long)i * a.plane + n], i, a.cs);
                 se -= (wgt(i) + d) * log1p(d * inv_wgt(i));
             }
-            acc[2] += se;
-            acc[3] += se * se;
+            double cnt = acc[0];
+            welford_add(cnt, acc[1], acc[2], pp);
+            welford_add(acc[0], acc[3], acc[4], se);
         }
     }
     __shared__ double sm[kDiagExtParts][kDiagBlock];
@@ -619,10 +667,8 @@ diag_ext_partial(const typename C::S* __restrict__ src, double* __restrict__ par
     for (int k = 0; k < kDiagExtParts; ++k) sm[k][threadIdx.x] = acc[k];
     __syncthreads();
     for (int s = kDiagBlock / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) {
-#pragma unroll
-            for (int k = 0; k < kDiagExtParts; ++k) sm[k][threadIdx.x] += sm[k][threadIdx.x + s];
-        }
+        if (threadIdx.x < s)
+            diag_ext_fold(&sm[0][threadIdx.x], kDiagBlock, &sm[0][threadIdx.x + s], kDiagBlock);
         __syncthreads();
     }
     if (threadIdx.x == 0) {
@@ -631,11 +677,11 @@ diag_ext_partial(const typename C::S* __restrict__ src, double* __restrict__ par
     }
 }
 
-// Reduces part[nblocks][4] into out[4] = (mean P, std P, mean s, std s).
+// Reduces part[nblocks][5] into out[4] = (mean P, std P, mean s, std s).
 __global__ void diag_ext_final(const double* __restrict__ part, int nblocks,
                                double* __restrict__ out, long long total);
 
-// Reduces part[nblocks][10] (fixed order) into out[KBC_DIAG_N].
+// Reduces part[nblocks][11] (fixed order) into out[KBC_DIAG_N].
 __global__ void diag_final(const double* __restrict__ part, int nblocks, double* __restrict__ out,
                            long long total);
 

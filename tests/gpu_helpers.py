@@ -70,17 +70,18 @@ def windows(g0_fn, nx, ny, nodes_xy, steps, variant, beta, half=None, **kw):
     return np.array(out)
 
 
-def oracle_sensitivity(g0, variant, beta, steps, nthreads=16, seed=0, ref_uv=None):
+def oracle_sensitivity(g0, variant, beta, steps, nthreads=16, seed=0, ref_uv=None, **kw):
     """Relative velocity gap between the oracle run from g0 and from g0 with
     every population perturbed by at most one ulp (seeded).  No FP64
     implementation of the same method can be expected to agree with the
-    oracle more closely than this rounding-sensitivity floor."""
+    oracle more closely than this rounding-sensitivity floor.  kw: gamma
+    mode arguments of O.step."""
     rng = np.random.default_rng(seed)
     gp = g0 * (1.0 + np.finfo(np.float64).eps * rng.choice([-1.0, 0.0, 1.0], size=g0.shape))
-    b = O.step(gp, variant, beta, steps, nthreads=nthreads)
+    b = O.step(gp, variant, beta, steps, nthreads=nthreads, **kw)
     _, bx, by = O.macro(b)
     if ref_uv is None:
-        a = O.step(g0, variant, beta, steps, nthreads=nthreads)
+        a = O.step(g0, variant, beta, steps, nthreads=nthreads, **kw)
         _, ax, ay = O.macro(a)
     else:
         ax, ay = ref_uv

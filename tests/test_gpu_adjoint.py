@@ -27,11 +27,13 @@ def _case(n, seed, k0=2.0, urms=0.05):
 
 
 def _gpu_adjoint(variant, dtype, beta, rho, ux, uy, steps, K, objective, tx=None, ty=None,
-                 guard=None):
+                 guard=None, gamma=None):
     ny, nx = rho.shape
     lat = Lattice(nx, ny, variant=variant, beta=beta, dtype=dtype)
     if guard is not None:
         lat.set_guard(guard)
+    if gamma is not None:
+        lat.set_gamma(gamma)
     u = np.ascontiguousarray(np.stack((ux, uy)))
     tgt = np.ascontiguousarray(np.stack((tx, ty))) if objective == 1 else None
     g = np.empty((2, ny, nx))
@@ -49,6 +51,26 @@ def test_adjoint_matches_oracle_adjoint(variant, objective):
     rho, ux, uy, tx, ty = _case(n, 5)
     J, g, gb = _gpu_adjoint(variant, "f64", beta, rho, ux, uy, steps, 5, objective, tx, ty)
     Jo, gxo, gyo, gbo = O.adjoint(OV[variant], beta, rho, ux, uy, steps, objective, tx, ty)
+    assert J == pytest.approx(Jo, rel=1e-13)
+    go = np.stack((gxo, gyo))
+    assert np.max(np.abs(g - go)) <= 1e-9 * np.max(np.abs(go))
+    assert gb == pytest.approx(gbo, rel=1e-9)
+
+
+@pytest.mark.parametrize("objective", [0, 1])
+@pytest.mark.parametrize("variant", ["A", "B", "C", "D"])
+def test_fixed_gamma_adjoint_matches_oracle_adjoint(variant, objective):
+    """Regularised mode, gamma fixed at 1/beta (the regularised limit of
+    Sec. 4): the reverse sweep's fixed-gamma branch, including its beta
+    derivative through beta (gamma - 2), against the oracle's complex-step
+    sweep in the same mode (16x16, 12 steps, FP64: J to 1e-13, gradients to
+    1e-9)."""
+    n, steps, beta = 16, 12, 0.95
+    rho, ux, uy, tx, ty = _case(n, 7)
+    J, g, gb = _gpu_adjoint(variant, "f64", beta, rho, ux, uy, steps, 5, objective, tx, ty,
+                            gamma=1.0 / beta)
+    Jo, gxo, gyo, gbo = O.adjoint(OV[variant], beta, rho, ux, uy, steps, objective, tx, ty,
+                                  gamma_mode=1, gamma_fixed=1.0 / beta)
     assert J == pytest.approx(Jo, rel=1e-13)
     go = np.stack((gxo, gyo))
     assert np.max(np.abs(g - go)) <= 1e-9 * np.max(np.abs(go))
