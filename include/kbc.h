@@ -112,6 +112,46 @@ int kbc_set_allocator(kbc_alloc_fn alloc, kbc_free_fn release, void* user);
  * with the same arithmetic.  *out is NULL on failure. */
 int kbc_create(int nx, int ny, int variant, double beta, int dtype, kbc_handle* out);
 
+/* y-slab of a larger doubly periodic grid, for a domain split into
+ * horizontal slabs (one per GPU or per handle).  The paper runs one periodic
+ * grid; the split follows from the pull of Eq. Egeneral, which reaches one
+ * row up and one row down: a step of rows [y0, y0 + ny) needs, besides
+ * them, the three populations with b = +1 (i = 6, 7, 8) of row y0 - 1 and
+ * the three with b = -1 (i = 0, 1, 2) of row y0 + ny, taken periodically in
+ * the global grid.  The handle holds the ny interior rows plus a ghost row
+ * below and above; x stays periodic within the handle.  Interior rows are
+ * addressed as on a plain handle (kbc_init, kbc_set_populations,
+ * kbc_get_populations, kbc_probe, kbc_moments take [.][ny][nx] fields of the
+ * slab's own rows).  Before every step, each face's ghost row must be filled
+ * with kbc_halo_recv from the neighbouring slab's kbc_halo_send (the slab
+ * itself when it is the whole periodic grid); kbc_step then advances one
+ * step (nsteps <= 1, else KBC_ERR_ARG).  Ghost rows start at f = W.
+ * kbc_diagnostics, kbc_diagnostics_ext, kbc_init_grad and kbc_adjoint need
+ * rows beyond the ghost populations and give KBC_ERR_ARG on a slab handle.
+ * Same requirements as kbc_create, with nx * (ny + 2) <= 2^31 - 1. */
+int kbc_create_slab(int nx, int ny, int variant, double beta, int dtype, kbc_handle* out);
+
+/* Halo of one face of a y-slab handle, in the handle's storage encoding
+ * (the stored deviations, see enum kbc_dtype): [3][nx] elements of
+ * kbc_halo_bytes / 3 / nx bytes each, populations in increasing index.
+ *   kbc_halo_send(h, 0, buf): bottom interior row, populations 0, 1, 2
+ *     (moving down: the lower neighbour's face-1 ghost row);
+ *   kbc_halo_send(h, 1, buf): top interior row, populations 6, 7, 8
+ *     (moving up: the upper neighbour's face-0 ghost row);
+ *   kbc_halo_recv(h, 0, buf): into the ghost row below row 0, populations
+ *     6, 7, 8 (what the lower neighbour sent through its face 1);
+ *   kbc_halo_recv(h, 1, buf): into the ghost row above row ny - 1,
+ *     populations 0, 1, 2 (what the upper neighbour sent through face 0).
+ * buf: host or device memory (KBC_ERR_ARG if NULL); device buffers are
+ * asynchronous on the handle's stream, host buffers synchronise it.
+ * KBC_ERR_ARG on a plain handle or a face other than 0 and 1;
+ * kbc_halo_send before the field is initialised gives KBC_ERR_STATE. */
+int kbc_halo_send(kbc_handle h, int face, void* buf);
+int kbc_halo_recv(kbc_handle h, int face, const void* buf);
+
+/* Bytes of one face's halo (3 nx stored elements). */
+int kbc_halo_bytes(kbc_handle h, size_t* bytes);
+
 /* Free the handle's device buffers (after synchronising its stream). */
 int kbc_destroy(kbc_handle h);
 

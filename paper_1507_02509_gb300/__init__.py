@@ -76,11 +76,13 @@ class Lattice:
 
     variant: "lbgk" or "A".."D" (Table 1); dtype: "f64", "f32" (float
     deviations f - W) or "f16" (scaled half deviations).  beta is the
-    relaxation parameter of Eq. Egeneral.
+    relaxation parameter of Eq. Egeneral.  slab=True makes the field ny rows
+    of a larger grid split into y-slabs, with ghost rows filled by halo
+    exchange between steps (kbc_create_slab; see slabs.py).
     """
 
     def __init__(self, nx: int, ny: int, variant="B", beta: float = 0.99, dtype="f32",
-                 stream=None, torch_allocator: bool = True):
+                 stream=None, torch_allocator: bool = True, slab: bool = False):
         import torch
 
         if not torch.cuda.is_available():
@@ -94,7 +96,9 @@ class Lattice:
         self.beta = float(beta)
         self.device = torch.device("cuda", torch.cuda.current_device())
         self._stream = stream
-        self.h = capi.kbc_create(self.nx, self.ny, self.variant, self.beta, self.dtype)
+        self.slab = bool(slab)
+        create = capi.kbc_create_slab if self.slab else capi.kbc_create
+        self.h = create(self.nx, self.ny, self.variant, self.beta, self.dtype)
         self._bind_stream()
 
     # -- plumbing
@@ -239,3 +243,8 @@ class Lattice:
     @property
     def bytes_per_update(self) -> float:
         return capi.kbc_bytes_per_update(self.h)
+
+    @property
+    def halo_bytes(self) -> int:
+        """Bytes of one face's halo of a y-slab handle ([3][nx] stored elements)."""
+        return capi.kbc_halo_bytes(self.h)

@@ -38,6 +38,10 @@ FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void
 SIGNATURES = {
     "kbc_set_allocator": (_i, [ALLOC_FN, FREE_FN, _vp]),
     "kbc_create": (_i, [_i, _i, _i, _d, _i, ctypes.POINTER(_vp)]),
+    "kbc_create_slab": (_i, [_i, _i, _i, _d, _i, ctypes.POINTER(_vp)]),
+    "kbc_halo_send": (_i, [_vp, _i, _vp]),
+    "kbc_halo_recv": (_i, [_vp, _i, _vp]),
+    "kbc_halo_bytes": (_i, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
     "kbc_destroy": (_i, [_vp]),
     "kbc_set_stream": (_i, [_vp, _vp]),
     "kbc_set_gamma_mode": (_i, [_vp, _i, _d]),
@@ -128,6 +132,27 @@ def kbc_create(nx: int, ny: int, variant: int, beta: float, dtype: int):
     check(None, load().kbc_create(int(nx), int(ny), int(variant), float(beta), int(dtype),
                                   ctypes.byref(h)))
     return h
+
+
+def kbc_create_slab(nx: int, ny: int, variant: int, beta: float, dtype: int):
+    h = ctypes.c_void_p()
+    check(None, load().kbc_create_slab(int(nx), int(ny), int(variant), float(beta), int(dtype),
+                                       ctypes.byref(h)))
+    return h
+
+
+def kbc_halo_send(h, face: int, buf):
+    return check(h, load().kbc_halo_send(h, int(face), ptr(buf)))
+
+
+def kbc_halo_recv(h, face: int, buf):
+    return check(h, load().kbc_halo_recv(h, int(face), ptr(buf)))
+
+
+def kbc_halo_bytes(h) -> int:
+    b = ctypes.c_size_t()
+    check(h, load().kbc_halo_bytes(h, ctypes.byref(b)))
+    return b.value
 
 
 def kbc_destroy(h):

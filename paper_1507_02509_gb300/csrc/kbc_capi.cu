@@ -117,6 +117,10 @@ struct kbc_ctx {
     float f16_scale = 1.0f;
     long long plane = 0;  // elements per population plane
     size_t elem = 8;      // bytes per stored element
+    // y-slab handle: each plane holds a ghost row below and above the ny
+    // interior rows; buf[k] points at interior row 0 of allocation alloc[k]
+    bool slab = false;
+    void* alloc[2] = {nullptr, nullptr};
     void* buf[2] = {nullptr, nullptr};
     int cur = 0;          // buffer holding the current state
     int* fix = nullptr;   // [0..1] counters, [64..] list of node indices
@@ -217,7 +221,13 @@ StepArgs args_of(const kbc_ctx* h)
     a.fix_list = h->fix ? h->fix + 64 : nullptr;
     a.fix_slot = h->fix_slot;
     a.flag = h->flag_dev;
+    a.ywrap = h->slab ? 0 : 1;
     return a;
+}
+
+int reject_slab(kbc_ctx* h, const char* what)
+{
+    return fail(h, KBC_ERR_ARG, std::string(what) + " is not available on a y-slab handle");
 }
 
 // Stage `bytes` from a host or device pointer into device memory.
@@ -579,11 +589,12 @@ int kbc_set_allocator(kbc_alloc_fn alloc, kbc_free_fn release, void* user)
     return KBC_OK;
 }
 
-int kbc_create(int nx, int ny, int variant, double beta, int dtype, kbc_handle* out)
+static int create_common(int nx, int ny, int variant, double beta, int dtype, bool slab,
+                         kbc_handle* out)
 {
     if (!out) return fail(nullptr, KBC_ERR_ARG, "out is NULL");
     *out = nullptr;
-    if (nx < 1 || ny < 1 || (long long)nx * ny > 2147483647LL)
+    if (nx < 1 || ny < 1 || (long long)nx * (ny + (slab ? 2 : 0)) > 2147483647LL)
         return fail(nullptr, KBC_ERR_ARG, "grid size out of range");
     if (!(beta > 0.0 && beta <= 1.0)) return fail(nullptr, KBC_ERR_ARG, "beta must lie in (0, 1]");
     if (variant < KBC_LBGK || variant > KBC_D) return fail(nullptr, KBC_ERR_ARG, "bad variant");
@@ -596,6 +607,7 @@ int kbc_create(int nx, int ny, int variant, double beta, int dtype, kbc_handle* 
     }
     h->nx = nx;
     h->ny = ny;
+    h->slab = slab;
     h->variant = variant;
     h->beta = beta;
     h->dtype = dtype;
@@ -610,10 +622,14 @@ int kbc_create(int nx, int ny, int variant, double beta, int dtype, kbc_handle* 
         return fail(nullptr, KBC_ERR_CUDA, m);
     }
     const long long per = 256 / (long long)h->elem;
-    h->plane = (((long long)nx * ny + per - 1) / per) * per;
+    const long long rows = (long long)ny + (slab ? 2 : 0);
+    h->plane = (((long long)nx * rows + per - 1) / per) * per;
     const size_t field = (size_t)9 * h->plane * h->elem;
-    h->buf[0] = dev_alloc(h, field);
-    h->buf[1] = dev_alloc(h, field);
+    for (int k = 0; k < 2; ++k) {
+        h->alloc[k] = dev_alloc(h, field);
+        h->buf[k] = h->alloc[k] && slab ? static_cast<char*>(h->alloc[k]) + (size_t)nx * h->elem
+                                        : h->alloc[k];
+    }
     h->flag_dev = static_cast<int*>(dev_alloc(h, 256));
     const long long total = (long long)nx * ny;
     h->diag_nblocks = diag_blocks(total, h->num_sms);
@@ -636,6 +652,8 @@ int kbc_create(int nx, int ny, int variant, double beta, int dtype, kbc_handle* 
     h->flag_host[0] = h->flag_host[1] = h->flag_host[2] = h->flag_host[3] = 0;
     e = cudaMemsetAsync(h->flag_dev, 0, 256, h->stream);
     if (e == cudaSuccess && h->fix) e = cudaMemsetAsync(h->fix, 0, 64 * sizeof(int), h->stream);
+    // ghost rows start at f = W (zero deviation) until the first halo arrives
+    for (int k = 0; k < 2 && slab && e == cudaSuccess; ++k) e = cudaMemsetAsync(h->alloc[k], 0, field, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) {
         std::string m = std::string("initial memset: ") + cudaGetErrorString(e);
@@ -646,13 +664,23 @@ int kbc_create(int nx, int ny, int variant, double beta, int dtype, kbc_handle* 
     return KBC_OK;
 }
 
+int kbc_create(int nx, int ny, int variant, double beta, int dtype, kbc_handle* out)
+{
+    return create_common(nx, ny, variant, beta, dtype, false, out);
+}
+
+int kbc_create_slab(int nx, int ny, int variant, double beta, int dtype, kbc_handle* out)
+{
+    return create_common(nx, ny, variant, beta, dtype, true, out);
+}
+
 int kbc_destroy(kbc_handle h)
 {
     if (!h) return KBC_ERR_ARG;
     cudaSetDevice(h->device);
     cudaStreamSynchronize(h->stream);
-    dev_free(h, h->buf[0]);
-    dev_free(h, h->buf[1]);
+    dev_free(h, h->alloc[0]);
+    dev_free(h, h->alloc[1]);
     dev_free(h, h->fix);
     dev_free(h, h->flag_dev);
     dev_free(h, h->diag_part);
@@ -757,6 +785,7 @@ int kbc_init(kbc_handle h, const double* rho, const double* u)
 
 int kbc_init_grad(kbc_handle h, const double* rho, const double* u)
 {
+    if (h && h->slab) return reject_slab(h, "kbc_init_grad (y gradients across the slab faces)");
     return init_common(h, rho, u, true);
 }
 
@@ -799,6 +828,8 @@ int kbc_step(kbc_handle h, int nsteps)
     int rc = check_h(h);
     if (rc) return rc;
     if (nsteps < 0) return fail(h, KBC_ERR_ARG, "nsteps must be >= 0");
+    if (h->slab && nsteps > 1)
+        return fail(h, KBC_ERR_ARG, "a y-slab handle steps once between halo exchanges (nsteps <= 1)");
     if (!h->initialized) return fail(h, KBC_ERR_STATE, "field not initialised");
     if (h->flag_host[0] & 2) return fail(h, KBC_ERR_TIMEOUT, "a device-side wait ran out");
     if (h->flag_host[0]) return fail(h, KBC_ERR_NONFINITE, "non-finite populations detected");
@@ -960,6 +991,7 @@ int kbc_diagnostics(kbc_handle h, double* out)
 {
     int rc = check_h(h);
     if (rc) return rc;
+    if (h->slab) return reject_slab(h, "kbc_diagnostics");
     if (!out) return fail(h, KBC_ERR_ARG, "NULL output");
     if (!h->initialized) return fail(h, KBC_ERR_STATE, "field not initialised");
     StepArgs a = args_of(h);
@@ -980,6 +1012,7 @@ int kbc_adjoint(kbc_handle h, const double* rho0, const double* u0, int nsteps, 
 {
     int rc = check_h(h);
     if (rc) return rc;
+    if (h->slab) return reject_slab(h, "kbc_adjoint");
     if (!rho0 || !u0 || !J || !grad_u0 || !grad_beta) return fail(h, KBC_ERR_ARG, "NULL argument");
     if (nsteps < 0 || ckpt_every < 1) return fail(h, KBC_ERR_ARG, "nsteps >= 0, ckpt_every >= 1");
     if (objective != 0 && objective != 1) return fail(h, KBC_ERR_ARG, "objective must be 0 or 1");
@@ -1191,6 +1224,7 @@ int kbc_diagnostics_ext(kbc_handle h, double* out)
 {
     int rc = check_h(h);
     if (rc) return rc;
+    if (h->slab) return reject_slab(h, "kbc_diagnostics_ext");
     if (!out) return fail(h, KBC_ERR_ARG, "NULL output");
     if (!h->initialized) return fail(h, KBC_ERR_STATE, "field not initialised");
     StepArgs a = args_of(h);
@@ -1203,6 +1237,52 @@ int kbc_diagnostics_ext(kbc_handle h, double* out)
     e = cudaMemcpyAsync(out, h->diag_out, KBC_DIAG_EXT_N * sizeof(double), cudaMemcpyDefault, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "diagnostics copy");
     return wait_stream(h, 0);
+}
+
+// Rows of the halo of one face: the first of the three populations and the
+// row (relative to interior row 0) in the current field.
+static void halo_rows(const kbc_ctx* h, int face, bool ghost, int* pop0, long long* row)
+{
+    if (!ghost) {
+        // outgoing: the bottom row's b = -1 populations, the top row's b = +1
+        *pop0 = face == 0 ? 0 : 6;
+        *row = face == 0 ? 0 : h->ny - 1;
+    } else {
+        // incoming: the lower ghost row's b = +1 populations, the upper's b = -1
+        *pop0 = face == 0 ? 6 : 0;
+        *row = face == 0 ? -1 : h->ny;
+    }
+}
+
+static int halo_copy(kbc_handle h, int face, void* out, const void* in)
+{
+    int rc = check_h(h);
+    if (rc) return rc;
+    if (!h->slab) return fail(h, KBC_ERR_ARG, "halo exchange needs a y-slab handle (kbc_create_slab)");
+    if (face != 0 && face != 1) return fail(h, KBC_ERR_ARG, "face must be 0 (lower) or 1 (upper)");
+    if (!(out ? (const void*)out : in)) return fail(h, KBC_ERR_ARG, "NULL buffer");
+    if (out && !h->initialized) return fail(h, KBC_ERR_STATE, "field not initialised");
+    int pop0;
+    long long row;
+    halo_rows(h, face, in != nullptr, &pop0, &row);
+    char* field = static_cast<char*>(h->buf[h->cur]) + ((long long)pop0 * h->plane + row * h->nx) * (long long)h->elem;
+    const size_t width = (size_t)h->nx * h->elem, pitch = (size_t)h->plane * h->elem;
+    cudaError_t e = out ? cudaMemcpy2DAsync(out, width, field, pitch, width, 3, cudaMemcpyDefault, h->stream)
+                        : cudaMemcpy2DAsync(field, pitch, in, width, width, 3, cudaMemcpyDefault, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "halo copy");
+    const bool host = !is_device_ptr(out ? (const void*)out : in);
+    return host ? wait_stream(h, 0) : KBC_OK;
+}
+
+int kbc_halo_send(kbc_handle h, int face, void* buf) { return halo_copy(h, face, buf, nullptr); }
+
+int kbc_halo_recv(kbc_handle h, int face, const void* buf) { return halo_copy(h, face, nullptr, buf); }
+
+int kbc_halo_bytes(kbc_handle h, size_t* bytes)
+{
+    if (!h || !bytes) return KBC_ERR_ARG;
+    *bytes = (size_t)3 * h->nx * h->elem;
+    return KBC_OK;
 }
 
 int kbc_bytes_per_update(kbc_handle h, double* bytes)

@@ -26,7 +26,17 @@ struct StepArgs {
     int* fix_list;       // node indices recorded for the FP64 re-evaluation
     int fix_slot;        // counter used by this step
     int* flag;           // set to 1 when a node's density is not finite
+    int ywrap;           // 1: periodic in y; 0: a y-slab whose rows -1 and ny are
+                         // ghost rows holding the neighbouring slabs' populations
 };
+
+// Source row of a pull that lands on row sy (y - b, so -1 <= sy <= ny):
+// periodic wrap, or on a y-slab the ghost row itself.
+__device__ __forceinline__ int pull_row(int sy, const StepArgs& a)
+{
+    if (!a.ywrap) return sy;
+    return sy < 0 ? sy + a.ny : (sy >= a.ny ? sy - a.ny : sy);
+}
 
 // ---------------------------------------------------------------- vectors
 
@@ -160,8 +170,8 @@ step_rows(const typename C::S* __restrict__ src, typename C::S* __restrict__ dst
         a.fix_count[a.fix_slot ^ 1] = 0;  // free the other counter for the next step
     if (x0 >= a.nx) return;               // whole warps only (nx % (32 NV) == 0)
     const int lane = threadIdx.x & 31;
-    const int ym = (y == 0) ? a.ny - 1 : y - 1;
-    const int yp = (y == a.ny - 1) ? 0 : y + 1;
+    const int ym = pull_row(y - 1, a);
+    const int yp = pull_row(y + 1, a);
     const int xl = (x0 == 0) ? a.nx - 1 : x0 - 1;
     const int xr = (x0 + NV == a.nx) ? 0 : x0 + NV;
 
@@ -246,7 +256,7 @@ step_nodes(const typename C::S* __restrict__ src, typename C::S* __restrict__ ds
             const int ai = i % 3 - 1, bi = i / 3 - 1;
             int sx = x - ai, sy = y - bi;
             sx = sx < 0 ? sx + a.nx : (sx >= a.nx ? sx - a.nx : sx);
-            sy = sy < 0 ? sy + a.ny : (sy >= a.ny ? sy - a.ny : sy);
+            sy = pull_row(sy, a);
             f[i] = C::load(__ldg(src + (long long)i * a.plane + (long long)sy * a.nx + sx), i, a.cs);
         }
         T rho;
@@ -283,7 +293,7 @@ step_nodes_f64(const typename C::S* __restrict__ src, typename C::S* __restrict_
             const int ai = i % 3 - 1, bi = i / 3 - 1;
             int sx = x - ai, sy = y - bi;
             sx = sx < 0 ? sx + a.nx : (sx >= a.nx ? sx - a.nx : sx);
-            sy = sy < 0 ? sy + a.ny : (sy >= a.ny ? sy - a.ny : sy);
+            sy = pull_row(sy, a);
             f[i] = C::to_f64(src[(long long)i * a.plane + (long long)sy * a.nx + sx], i, a.cs);
         }
         double rho;
@@ -319,7 +329,7 @@ step_fixup(const typename C::S* __restrict__ src, typename C::S* __restrict__ ds
             const int ai = i % 3 - 1, bi = i / 3 - 1;
             int sx = x - ai, sy = y - bi;
             sx = sx < 0 ? sx + a.nx : (sx >= a.nx ? sx - a.nx : sx);
-            sy = sy < 0 ? sy + a.ny : (sy >= a.ny ? sy - a.ny : sy);
+            sy = pull_row(sy, a);
             f[i] = C::to_f64(src[(long long)i * a.plane + (long long)sy * a.nx + sx], i, a.cs);
         }
         CollideParams<double> q = a.pd;

@@ -115,8 +115,8 @@ __device__ __forceinline__ void tma_issue(const S* __restrict__ src, S* buf, uin
     constexpr int ROW = TX + 2 * H;
     const int y = t / tiles_per_row;
     const int x0 = (t - y * tiles_per_row) * TX;
-    const int ym = (y == 0) ? a.ny - 1 : y - 1;
-    const int yp = (y == a.ny - 1) ? 0 : y + 1;
+    const int ym = pull_row(y - 1, a);
+    const int yp = pull_row(y + 1, a);
     mbar_expect_tx(bar, tma_stage_tx_bytes<S, TX>());
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
