@@ -270,6 +270,12 @@ __device__ __forceinline__ double adj_node_f64(const typename C::S* __restrict__
 
 // lambda^n from lambda^{n+1} and the forward state g^n; beta adjoint summed
 // into part[blockIdx.x] (same grid every step, so the sum order is fixed).
+// One node per thread; the grid strides over row segments of kAdjBlock
+// nodes, so a thread finds its row and column once per segment and the
+// offsets of the pull's source rows (y - b) and columns (x - a) once per
+// node: every population's load and store address is the node's own plus
+// a plane offset, a row offset and a column offset (consecutive threads
+// touch consecutive columns).
 // Single precision: a node whose entropic denominator is at or below the
 // guard (the nodes the forward step re-evaluates in double) is marked in
 // fixmask (bit n % 32 of word n / 32) and left to adj_fixup, which redoes it
@@ -282,20 +288,30 @@ adj_step(const typename C::S* __restrict__ g, const typename C::T* __restrict__ 
 {
     using T = typename C::T;
     const CollideParams<T>& p = params_of<T>(a);
-    const long long total = (long long)a.nx * a.ny;
+    const int nbx = (a.nx + kAdjBlock - 1) / kAdjBlock;
+    const int segs = nbx * a.ny;  // nx * ny < 2^31
     double bsum = 0.0;
-    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < total;
-         n += (long long)gridDim.x * blockDim.x) {
-        const int y = (int)(n / a.nx), x = (int)(n - (long long)y * a.nx);
+    for (int sg = blockIdx.x; sg < segs; sg += gridDim.x) {
+        const int y = sg / nbx;
+        const int x = (sg - y * nbx) * kAdjBlock + (int)threadIdx.x;
+        if (x >= a.nx) continue;
+        // offsets of the source rows y - b (b = +1, -1; periodic: the same
+        // for the whole segment) and of the source columns x - a (a = +1,
+        // -1; they differ from -a only at the row ends)
+        const long long dn = (y == 0) ? (long long)(a.ny - 1) * a.nx : -(long long)a.nx;
+        const long long up = (y == a.ny - 1) ? -(long long)(a.ny - 1) * a.nx : (long long)a.nx;
+        const int cl = (x == 0) ? a.nx - 1 : -1;
+        const int cr = (x == a.nx - 1) ? 1 - a.nx : 1;
+        const long long n = (long long)y * a.nx + x;
+        const typename C::S* gn = g + n;
+        T* ln = lam_out + n;
         T d[9], lam[9], mu[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             const int ai = i % 3 - 1, bi = i / 3 - 1;
-            int sx = x - ai, sy = y - bi;
-            sx = sx < 0 ? sx + a.nx : (sx >= a.nx ? sx - a.nx : sx);
-            sy = sy < 0 ? sy + a.ny : (sy >= a.ny ? sy - a.ny : sy);
-            const long long src = (long long)sy * a.nx + sx;
-            d[i] = C::decode(g[(long long)i * a.plane + src], i, a.cs);
+            const long long off = (long long)i * a.plane + (bi == 1 ? dn : (bi == -1 ? up : 0)) +
+                                  (ai == 1 ? cl : (ai == -1 ? cr : 0));
+            d[i] = C::decode(gn[off], i, a.cs);
             lam[i] = lam_in[(long long)i * a.plane + n];
         }
         T bbar;
@@ -310,10 +326,9 @@ adj_step(const typename C::S* __restrict__ g, const typename C::T* __restrict__ 
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             const int ai = i % 3 - 1, bi = i / 3 - 1;
-            int sx = x - ai, sy = y - bi;
-            sx = sx < 0 ? sx + a.nx : (sx >= a.nx ? sx - a.nx : sx);
-            sy = sy < 0 ? sy + a.ny : (sy >= a.ny ? sy - a.ny : sy);
-            lam_out[(long long)i * a.plane + (long long)sy * a.nx + sx] = mu[i];
+            const long long off = (long long)i * a.plane + (bi == 1 ? dn : (bi == -1 ? up : 0)) +
+                                  (ai == 1 ? cl : (ai == -1 ? cr : 0));
+            ln[off] = mu[i];
         }
     }
     block_add(bsum, part + blockIdx.x);
