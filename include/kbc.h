@@ -351,6 +351,17 @@ int kbc_adjoint(kbc_handle h, const double* rho0, const double* u0, int nsteps, 
  * storage (9 reads + 9 writes), for roofline accounting. */
 int kbc_bytes_per_update(kbc_handle h, double* bytes);
 
+/* Measured issue rate of double-precision fused multiply-adds on the
+ * current device, the ceiling of the FP64-storage path, whose step is bound
+ * by the FP64 pipe rather than by memory (a measurement helper for roofline
+ * accounting; the paper has no counterpart).  Launches a kernel of
+ * independent DFMA chains filling every SM on `stream` (a cudaStream_t,
+ * NULL = legacy default) four times, times each with CUDA events and writes
+ * the best rate, in thread DFMA operations per second, to *dfma_per_s.
+ * Synchronises the stream.  Errors: KBC_ERR_ARG (NULL output),
+ * KBC_ERR_CUDA. */
+int kbc_fp64_fma_rate(void* stream, double* dfma_per_s);
+
 /* Message describing the last error on h (or of the last kbc_create when h
  * is NULL).  Valid until the next call on h. */
 const char* kbc_last_error(kbc_handle h);

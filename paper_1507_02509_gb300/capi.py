@@ -65,6 +65,7 @@ SIGNATURES = {
     "kbc_adjoint": (_i, [_vp, _vp, _vp, _i, _i, _i, _vp, ctypes.POINTER(_d), _vp,
                          ctypes.POINTER(_d)]),
     "kbc_bytes_per_update": (_i, [_vp, ctypes.POINTER(_d)]),
+    "kbc_fp64_fma_rate": (_i, [_vp, ctypes.POINTER(_d)]),
     "kbc_last_error": (ctypes.c_char_p, [_vp]),
 }
 
@@ -259,6 +260,15 @@ def kbc_bytes_per_update(h) -> float:
     b = ctypes.c_double()
     check(h, load().kbc_bytes_per_update(h, ctypes.byref(b)))
     return b.value
+
+
+def kbc_fp64_fma_rate(stream=None) -> float:
+    """Measured thread DFMA operations per second of the current device."""
+    r = ctypes.c_double()
+    st = load().kbc_fp64_fma_rate(stream, ctypes.byref(r))
+    if st != KBC_OK:
+        raise KBCError(st, "kbc_fp64_fma_rate failed")
+    return r.value
 
 
 def kbc_last_error(h) -> str:

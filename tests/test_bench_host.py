@@ -69,3 +69,19 @@ def test_roofline_kernel_name_and_traffic_record():
     assert bench.traffic_from_profile("step_rows<C,f32>", "f32", n) is None
     assert bench.traffic_from_profile("step_tma<B,f32>", "f32", n) is None
     assert bench.traffic_from_profile("step_tma<B,f16>", "f16", n) is None
+
+
+def test_fp64_ops_record_applies_to_its_kernel_only():
+    """The FP64 path's roofline uses the committed FP64 instruction count only
+    for the kernel it was captured on, on the current sources."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    ops = bench.fp64_ops_from_profile("step_rows<B,f64>")
+    with open(os.path.join(ROOT, "profiles", "kbc_step_rows_f64_ops.txt")) as f:
+        current = f"kernel_source_hash: {bench.kernel_source_hash()}" in f.read()
+    if current:
+        assert ops is not None and 150 < ops < 260
+    else:
+        assert ops is None
+    assert bench.fp64_ops_from_profile("step_rows<C,f64>") is None
