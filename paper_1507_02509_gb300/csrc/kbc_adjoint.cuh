@@ -152,7 +152,7 @@ __device__ __forceinline__ bool collide_adjoint(const T (&d)[9], const T (&lam)[
             dsb[i] = shb * dh[i] * q[i];
             dhb[i] += shb * ds[i] * q[i] + T(2) * hhb * dh[i] * q[i];
             const T qb = shb * ds[i] * dh[i] + hhb * dh[i] * dh[i];
-            Pb[i] -= qb * q[i] * xi_inv[i];
+            Pb[i] -= qb * (q[i] * q[i]) * T(wgt(i));  // q_i / x_i = W_i q_i^2
             dfb[i] += dhb[i];
             dsb[i] -= dhb[i];
         }
@@ -204,11 +204,14 @@ __device__ __forceinline__ bool collide_adjoint(const T (&d)[9], const T (&lam)[
     T drhob = T(0), usqb = T(0);
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
+        // xi and P again from u (cheaper than keeping nine of each live)
+        const T xr = T(va(i)) * ux + T(vb(i)) * uy;
+        const T Pr = xr * (T(3) + T(4.5) * xr) - usq15;
         mu[i] = lam[i] + dfb[i];
-        drhob -= dfb[i] * T(wgt(i)) * (T(1) + P[i]);
+        drhob -= dfb[i] * T(wgt(i)) * (T(1) + Pr);
         Pb[i] -= dfb[i] * T(wgt(i)) * rho;
         usqb -= Pb[i];
-        const T xib = Pb[i] * (T(3) + T(9) * xi[i]);
+        const T xib = Pb[i] * (T(3) + T(9) * xr);
         uxb += T(va(i)) * xib;
         uyb += T(vb(i)) * xib;
     }
@@ -268,14 +271,54 @@ __device__ __forceinline__ double adj_node_f64(const typename C::S* __restrict__
     return bnode;
 }
 
+// Reverse step of one node: g, lam_in and lam_out point at the node's row
+// position minus t (t is added to every access), dn / up are the offsets of
+// the rows y - 1 / y + 1 and cl / cr those of the columns x - 1 / x + 1.
+// Writes lambda^n to the nine pull sources and returns the beta adjoint
+// (0 for a node left to the double redo, which it marks in fixmask).
+template <int VAR, class C>
+__device__ __forceinline__ double adj_node(const typename C::S* __restrict__ g,
+                                           const typename C::T* __restrict__ lam_in,
+                                           typename C::T* __restrict__ lam_out, int t, long long dn,
+                                           long long up, int cl, int cr, long long n,
+                                           unsigned* __restrict__ fixmask,
+                                           const CollideParams<typename C::T>& p, const StepArgs& a)
+{
+    using T = typename C::T;
+    T d[9], lam[9], mu[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const int ai = i % 3 - 1, bi = i / 3 - 1;
+        const long long off = (long long)i * a.plane + (bi == 1 ? dn : (bi == -1 ? up : 0)) +
+                              (ai == 1 ? cl : (ai == -1 ? cr : 0));
+        d[i] = C::decode(g[off + t], i, a.cs);
+        lam[i] = lam_in[(long long)i * a.plane + t];
+    }
+    T bbar;
+    const bool guarded = collide_adjoint<VAR>(d, lam, p, mu, bbar);
+    if constexpr (!std::is_same<T, double>::value && VAR != kLBGK) {
+        if (guarded) {
+            atomicOr(fixmask + (n >> 5), 1u << (n & 31));
+            bbar = T(0);  // summed by adj_fixup
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const int ai = i % 3 - 1, bi = i / 3 - 1;
+        const long long off = (long long)i * a.plane + (bi == 1 ? dn : (bi == -1 ? up : 0)) +
+                              (ai == 1 ? cl : (ai == -1 ? cr : 0));
+        lam_out[off + t] = mu[i];
+    }
+    return (double)bbar;
+}
+
 // lambda^n from lambda^{n+1} and the forward state g^n; beta adjoint summed
 // into part[blockIdx.x] (same grid every step, so the sum order is fixed).
 // One node per thread; the grid strides over row segments of kAdjBlock
-// nodes, so a thread finds its row and column once per segment and the
-// offsets of the pull's source rows (y - b) and columns (x - a) once per
-// node: every population's load and store address is the node's own plus
-// a plane offset, a row offset and a column offset (consecutive threads
-// touch consecutive columns).
+// nodes.  A segment away from the row ends addresses every population as
+// the segment's base plus an offset that is the same for the whole block
+// (plane, source row, source column) plus the thread index; the segments at
+// the row ends take the periodic wrap of the columns per thread.
 // Single precision: a node whose entropic denominator is at or below the
 // guard (the nodes the forward step re-evaluates in double) is marked in
 // fixmask (bit n % 32 of word n / 32) and left to adj_fixup, which redoes it
@@ -293,42 +336,26 @@ adj_step(const typename C::S* __restrict__ g, const typename C::T* __restrict__ 
     double bsum = 0.0;
     for (int sg = blockIdx.x; sg < segs; sg += gridDim.x) {
         const int y = sg / nbx;
-        const int x = (sg - y * nbx) * kAdjBlock + (int)threadIdx.x;
-        if (x >= a.nx) continue;
-        // offsets of the source rows y - b (b = +1, -1; periodic: the same
-        // for the whole segment) and of the source columns x - a (a = +1,
-        // -1; they differ from -a only at the row ends)
+        const int x0 = (sg - y * nbx) * kAdjBlock;
+        const int x = x0 + (int)threadIdx.x;
+        // offsets of the source rows y - b (b = +1, -1; periodic), the same
+        // for the whole segment
         const long long dn = (y == 0) ? (long long)(a.ny - 1) * a.nx : -(long long)a.nx;
         const long long up = (y == a.ny - 1) ? -(long long)(a.ny - 1) * a.nx : (long long)a.nx;
-        const int cl = (x == 0) ? a.nx - 1 : -1;
-        const int cr = (x == a.nx - 1) ? 1 - a.nx : 1;
-        const long long n = (long long)y * a.nx + x;
-        const typename C::S* gn = g + n;
-        T* ln = lam_out + n;
-        T d[9], lam[9], mu[9];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            const int ai = i % 3 - 1, bi = i / 3 - 1;
-            const long long off = (long long)i * a.plane + (bi == 1 ? dn : (bi == -1 ? up : 0)) +
-                                  (ai == 1 ? cl : (ai == -1 ? cr : 0));
-            d[i] = C::decode(gn[off], i, a.cs);
-            lam[i] = lam_in[(long long)i * a.plane + n];
-        }
-        T bbar;
-        const bool guarded = collide_adjoint<VAR>(d, lam, p, mu, bbar);
-        if constexpr (!std::is_same<T, double>::value && VAR != kLBGK) {
-            if (guarded) {
-                atomicOr(fixmask + (n >> 5), 1u << (n & 31));
-                bbar = T(0);  // summed by adj_fixup
-            }
-        }
-        bsum += (double)bbar;
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            const int ai = i % 3 - 1, bi = i / 3 - 1;
-            const long long off = (long long)i * a.plane + (bi == 1 ? dn : (bi == -1 ? up : 0)) +
-                                  (ai == 1 ? cl : (ai == -1 ? cr : 0));
-            ln[off] = mu[i];
+        if (x0 > 0 && x0 + kAdjBlock < a.nx) {
+            // interior segment: the source column of population i is x - a_i
+            // for every thread, so each address is the segment's base plus an
+            // offset shared by the block plus the thread index
+            const long long base = (long long)y * a.nx + x0;
+            bsum += adj_node<VAR, C>(g + base, lam_in + base, lam_out + base, (int)threadIdx.x, dn, up,
+                                     -1, 1, base + threadIdx.x, fixmask, p, a);
+        } else if (x < a.nx) {
+            // row ends: the columns x -+ 1 wrap
+            const long long base = (long long)y * a.nx + x;
+            const int cl = (x == 0) ? a.nx - 1 : -1;
+            const int cr = (x == a.nx - 1) ? 1 - a.nx : 1;
+            bsum += adj_node<VAR, C>(g + base, lam_in + base, lam_out + base, 0, dn, up, cl, cr, base,
+                                     fixmask, p, a);
         }
     }
     block_add(bsum, part + blockIdx.x);
