@@ -91,6 +91,8 @@ enum kbc_status {
 /* Number of doubles written by kbc_diagnostics and kbc_diagnostics_ext. */
 #define KBC_DIAG_N 10
 #define KBC_DIAG_EXT_N 4
+/* Number of doubles in one partial diagnostics set (kbc_diagnostics_partial). */
+#define KBC_DIAG_PART_N 11
 
 /* Device allocator hook: returns a device pointer of at least `bytes` bytes
  * (256-byte aligned) or NULL; `stream` is the handle's bound stream. */
@@ -126,31 +128,41 @@ int kbc_create(int nx, int ny, int variant, double beta, int dtype, kbc_handle* 
  * with kbc_halo_recv from the neighbouring slab's kbc_halo_send (the slab
  * itself when it is the whole periodic grid); kbc_step then advances one
  * step (nsteps <= 1, else KBC_ERR_ARG).  Ghost rows start at f = W.
+ * Global diagnostics of a split grid: kbc_diagnostics_partial per slab
+ * (after full halos), combined with kbc_diagnostics_merge.
  * kbc_diagnostics, kbc_diagnostics_ext, kbc_init_grad and kbc_adjoint need
- * rows beyond the ghost populations and give KBC_ERR_ARG on a slab handle.
- * Same requirements as kbc_create, with nx * (ny + 2) <= 2^31 - 1. */
+ * rows beyond the ghost rows or the whole grid and give KBC_ERR_ARG on a
+ * slab handle.  Same requirements as kbc_create, with
+ * nx * (ny + 2) <= 2^31 - 1. */
 int kbc_create_slab(int nx, int ny, int variant, double beta, int dtype, kbc_handle* out);
 
 /* Halo of one face of a y-slab handle, in the handle's storage encoding
- * (the stored deviations, see enum kbc_dtype): [3][nx] elements of
- * kbc_halo_bytes / 3 / nx bytes each, populations in increasing index.
- *   kbc_halo_send(h, 0, buf): bottom interior row, populations 0, 1, 2
- *     (moving down: the lower neighbour's face-1 ghost row);
- *   kbc_halo_send(h, 1, buf): top interior row, populations 6, 7, 8
- *     (moving up: the upper neighbour's face-0 ghost row);
- *   kbc_halo_recv(h, 0, buf): into the ghost row below row 0, populations
- *     6, 7, 8 (what the lower neighbour sent through its face 1);
- *   kbc_halo_recv(h, 1, buf): into the ghost row above row ny - 1,
- *     populations 0, 1, 2 (what the upper neighbour sent through face 0).
+ * (the stored deviations, see enum kbc_dtype), populations in increasing
+ * index, each an nx-element row.
+ *   full = 0: the three populations that cross the face, [3][nx] -- what a
+ *   step needs:
+ *     kbc_halo_send(h, 0, 0, buf): bottom interior row, populations 0, 1, 2
+ *       (moving down: the lower neighbour's face-1 ghost row);
+ *     kbc_halo_send(h, 1, 0, buf): top interior row, populations 6, 7, 8
+ *       (moving up: the upper neighbour's face-0 ghost row);
+ *     kbc_halo_recv(h, 0, 0, buf): into the ghost row below row 0,
+ *       populations 6, 7, 8 (what the lower neighbour sent through face 1);
+ *     kbc_halo_recv(h, 1, 0, buf): into the ghost row above row ny - 1,
+ *       populations 0, 1, 2 (what the upper neighbour sent through face 0).
+ *   full = 1: all nine populations of the same rows, [9][nx] -- what
+ *     kbc_diagnostics_partial needs in the ghost rows (the neighbouring
+ *     rows' velocity for the vorticity).
  * buf: host or device memory (KBC_ERR_ARG if NULL); device buffers are
  * asynchronous on the handle's stream, host buffers synchronise it.
- * KBC_ERR_ARG on a plain handle or a face other than 0 and 1;
- * kbc_halo_send before the field is initialised gives KBC_ERR_STATE. */
-int kbc_halo_send(kbc_handle h, int face, void* buf);
-int kbc_halo_recv(kbc_handle h, int face, const void* buf);
+ * KBC_ERR_ARG on a plain handle, a face other than 0 and 1 or full other
+ * than 0 and 1; kbc_halo_send before the field is initialised gives
+ * KBC_ERR_STATE. */
+int kbc_halo_send(kbc_handle h, int face, int full, void* buf);
+int kbc_halo_recv(kbc_handle h, int face, int full, const void* buf);
 
-/* Bytes of one face's halo (3 nx stored elements). */
-int kbc_halo_bytes(kbc_handle h, size_t* bytes);
+/* Bytes of one face's halo: 3 nx (full = 0) or 9 nx (full = 1) stored
+ * elements. */
+int kbc_halo_bytes(kbc_handle h, int full, size_t* bytes);
 
 /* Free the handle's device buffers (after synchronising its stream). */
 int kbc_destroy(kbc_handle h);
@@ -254,6 +266,27 @@ int kbc_moments(kbc_handle h, double* rho, double* u);
  *       performs (2 for LBGK)
  *   [8] spatial std of |u|^2/2   [9] spatial std of w^2/2 */
 int kbc_diagnostics(kbc_handle h, double* out);
+
+/* The diagnostics of this handle's nodes as one partial set, to be combined
+ * with other parts of the same grid (e.g. the slabs of a split grid, one per
+ * rank) by kbc_diagnostics_merge: out[KBC_DIAG_PART_N] on the host =
+ *   [0] sum rho  [1] sum rho u_x  [2] sum rho u_y  [3] node count
+ *   [4] mean and [5] sum of squared deviations of |u|^2/2
+ *   [6] mean and [7] sum of squared deviations of w^2/2
+ *   [8] sum, [9] min, [10] max of gamma
+ * with the definitions of kbc_diagnostics.  On a y-slab handle the ghost
+ * rows must hold full halos (kbc_halo_recv with full = 1) of the field's
+ * current state: the vorticity of the boundary rows and the gamma of the
+ * next step's collision read them.  Synchronises the handle's stream. */
+int kbc_diagnostics_partial(kbc_handle h, double* out);
+
+/* Combines n >= 1 partial sets parts[n][KBC_DIAG_PART_N] (in that order:
+ * sums added, means and sums of squared deviations by Chan, Golub and
+ * LeVeque's pairwise formula, minimum and maximum) into the KBC_DIAG_N
+ * values of kbc_diagnostics.  Host arithmetic only: no device, no handle.
+ * KBC_ERR_ARG for n < 1, NULL pointers or no nodes (message:
+ * kbc_last_error(NULL)). */
+int kbc_diagnostics_merge(int n, const double* parts, double* out);
 
 /* Further diagnostics of the paper's turbulence figures (FP64 device
  * reductions), out[KBC_DIAG_EXT_N] on the host:

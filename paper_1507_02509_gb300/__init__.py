@@ -248,3 +248,18 @@ class Lattice:
     def halo_bytes(self) -> int:
         """Bytes of one face's halo of a y-slab handle ([3][nx] stored elements)."""
         return capi.kbc_halo_bytes(self.h)
+
+    @property
+    def full_halo_bytes(self) -> int:
+        """Bytes of one face's full halo ([9][nx] stored elements)."""
+        return capi.kbc_halo_bytes(self.h, 1)
+
+    def diagnostics_partial(self):
+        """This handle's nodes as one partial diagnostics set (float64 numpy,
+        KBC_DIAG_PART_N values; combine with kbc_diagnostics_merge)."""
+        import numpy as np
+
+        self._bind_stream()
+        out = np.zeros(capi.KBC_DIAG_PART_N)
+        capi.kbc_diagnostics_partial(self.h, out)
+        return out

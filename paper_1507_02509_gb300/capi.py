@@ -22,6 +22,7 @@ KBC_OK, KBC_ERR_ARG, KBC_ERR_CUDA, KBC_ERR_NOMEM = 0, -1, -2, -3
 KBC_ERR_NONFINITE, KBC_ERR_TIMEOUT, KBC_ERR_STATE = -4, -5, -6
 KBC_DIAG_N = 10
 KBC_DIAG_EXT_N = 4
+KBC_DIAG_PART_N = 11
 KBC_KERNEL_AUTO, KBC_KERNEL_ROWS, KBC_KERNEL_NODES, KBC_KERNEL_BULK = 0, 1, 2, 3
 
 STATUS_NAMES = {
@@ -39,9 +40,9 @@ SIGNATURES = {
     "kbc_set_allocator": (_i, [ALLOC_FN, FREE_FN, _vp]),
     "kbc_create": (_i, [_i, _i, _i, _d, _i, ctypes.POINTER(_vp)]),
     "kbc_create_slab": (_i, [_i, _i, _i, _d, _i, ctypes.POINTER(_vp)]),
-    "kbc_halo_send": (_i, [_vp, _i, _vp]),
-    "kbc_halo_recv": (_i, [_vp, _i, _vp]),
-    "kbc_halo_bytes": (_i, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
+    "kbc_halo_send": (_i, [_vp, _i, _i, _vp]),
+    "kbc_halo_recv": (_i, [_vp, _i, _i, _vp]),
+    "kbc_halo_bytes": (_i, [_vp, _i, ctypes.POINTER(ctypes.c_size_t)]),
     "kbc_destroy": (_i, [_vp]),
     "kbc_set_stream": (_i, [_vp, _vp]),
     "kbc_set_gamma_mode": (_i, [_vp, _i, _d]),
@@ -60,6 +61,8 @@ SIGNATURES = {
     "kbc_moments": (_i, [_vp, _vp, _vp]),
     "kbc_diagnostics": (_i, [_vp, _vp]),
     "kbc_diagnostics_ext": (_i, [_vp, _vp]),
+    "kbc_diagnostics_partial": (_i, [_vp, _vp]),
+    "kbc_diagnostics_merge": (_i, [_i, _vp, _vp]),
     "kbc_spectrum": (_i, [_i, _vp, _i, _vp, _vp, _vp]),
     "kbc_diagnostics_noalloc": (_i, [_i, _i, _i, _d, _vp, _vp, _vp]),
     "kbc_adjoint": (_i, [_vp, _vp, _vp, _i, _i, _i, _vp, ctypes.POINTER(_d), _vp,
@@ -142,17 +145,17 @@ def kbc_create_slab(nx: int, ny: int, variant: int, beta: float, dtype: int):
     return h
 
 
-def kbc_halo_send(h, face: int, buf):
-    return check(h, load().kbc_halo_send(h, int(face), ptr(buf)))
+def kbc_halo_send(h, face: int, buf, full: int = 0):
+    return check(h, load().kbc_halo_send(h, int(face), int(full), ptr(buf)))
 
 
-def kbc_halo_recv(h, face: int, buf):
-    return check(h, load().kbc_halo_recv(h, int(face), ptr(buf)))
+def kbc_halo_recv(h, face: int, buf, full: int = 0):
+    return check(h, load().kbc_halo_recv(h, int(face), int(full), ptr(buf)))
 
 
-def kbc_halo_bytes(h) -> int:
+def kbc_halo_bytes(h, full: int = 0) -> int:
     b = ctypes.c_size_t()
-    check(h, load().kbc_halo_bytes(h, ctypes.byref(b)))
+    check(h, load().kbc_halo_bytes(h, int(full), ctypes.byref(b)))
     return b.value
 
 
@@ -228,6 +231,14 @@ def kbc_diagnostics(h, out):
 
 def kbc_diagnostics_ext(h, out):
     return check(h, load().kbc_diagnostics_ext(h, ptr(out)))
+
+
+def kbc_diagnostics_partial(h, out):
+    return check(h, load().kbc_diagnostics_partial(h, ptr(out)))
+
+
+def kbc_diagnostics_merge(n: int, parts, out):
+    return check(None, load().kbc_diagnostics_merge(int(n), ptr(parts), ptr(out)))
 
 
 def kbc_spectrum(n: int, u, nbins: int, E, Z, stream=None):

@@ -19,7 +19,7 @@
 namespace kbc {
 
 __global__ void diag_final(const double* __restrict__ part, int nblocks, double* __restrict__ out,
-                           long long total)
+                           long long total, int raw)
 {
     // one block; thread t folds blocks t, t + blockDim, ... in a fixed order,
     // then a fixed tree combines the threads
@@ -34,7 +34,10 @@ __global__ void diag_final(const double* __restrict__ part, int nblocks, double*
         if (threadIdx.x < s) diag_fold(&sm[0][threadIdx.x], kDiagBlock, &sm[0][threadIdx.x + s], kDiagBlock);
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && raw) {
+#pragma unroll
+        for (int k = 0; k < kDiagParts; ++k) out[k] = sm[k][0];
+    } else if (threadIdx.x == 0) {
         out[0] = sm[0][0];
         out[1] = sm[1][0];
         out[2] = sm[2][0];
@@ -998,12 +1001,73 @@ int kbc_diagnostics(kbc_handle h, double* out)
     cudaError_t e = by_codec(h->dtype, [&](auto c) {
         using C = decltype(c);
         return launch_diag<C>(h->buf[h->cur], h->diag_part, h->diag_nblocks, h->diag_out,
-                              h->variant, a, h->stream);
+                              h->variant, a, h->stream, 0);
     });
     if (e != cudaSuccess) return cuda_fail(h, e, "diagnostics launch");
     e = cudaMemcpyAsync(out, h->diag_out, KBC_DIAG_N * sizeof(double), cudaMemcpyDefault, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "diagnostics copy");
     return wait_stream(h, 0);
+}
+
+int kbc_diagnostics_partial(kbc_handle h, double* out)
+{
+    int rc = check_h(h);
+    if (rc) return rc;
+    if (!out) return fail(h, KBC_ERR_ARG, "NULL output");
+    if (!h->initialized) return fail(h, KBC_ERR_STATE, "field not initialised");
+    StepArgs a = args_of(h);
+    cudaError_t e = by_codec(h->dtype, [&](auto c) {
+        using C = decltype(c);
+        return launch_diag<C>(h->buf[h->cur], h->diag_part, h->diag_nblocks, h->diag_out,
+                              h->variant, a, h->stream, 1);
+    });
+    if (e != cudaSuccess) return cuda_fail(h, e, "diagnostics launch");
+    e = cudaMemcpyAsync(out, h->diag_out, KBC_DIAG_PART_N * sizeof(double), cudaMemcpyDefault,
+                        h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "diagnostics copy");
+    return wait_stream(h, 0);
+}
+
+int kbc_diagnostics_merge(int n, const double* parts, double* out)
+{
+    if (n < 1 || !parts || !out) return fail(nullptr, KBC_ERR_ARG, "merge: bad argument");
+    // Chan, Golub and LeVeque's pairwise combination of the (count, mean,
+    // M2) sets, the sums added, min and max taken, in the order given
+    double acc[KBC_DIAG_PART_N];
+    for (int k = 0; k < KBC_DIAG_PART_N; ++k) acc[k] = parts[k];
+    for (int j = 1; j < n; ++j) {
+        const double* b = parts + (size_t)j * KBC_DIAG_PART_N;
+        const double na = acc[3], nb = b[3], nn = na + nb;
+        acc[0] += b[0];
+        acc[1] += b[1];
+        acc[2] += b[2];
+        for (int k = 4; k <= 6 && nb > 0.0; k += 2) {
+            if (na == 0.0) {
+                acc[k] = b[k];
+                acc[k + 1] = b[k + 1];
+            } else {
+                const double dlt = b[k] - acc[k];
+                acc[k] += dlt * (nb / nn);
+                acc[k + 1] += b[k + 1] + dlt * dlt * (na * nb / nn);
+            }
+        }
+        acc[3] = nn;
+        acc[8] += b[8];
+        acc[9] = std::fmin(acc[9], b[9]);
+        acc[10] = std::fmax(acc[10], b[10]);
+    }
+    if (!(acc[3] > 0.0)) return fail(nullptr, KBC_ERR_ARG, "merge: no nodes");
+    out[0] = acc[0];
+    out[1] = acc[1];
+    out[2] = acc[2];
+    out[3] = acc[4];
+    out[4] = acc[6];
+    out[5] = acc[8] / acc[3];
+    out[6] = acc[9];
+    out[7] = acc[10];
+    out[8] = std::sqrt(std::fmax(acc[5], 0.0) / acc[3]);
+    out[9] = std::sqrt(std::fmax(acc[7], 0.0) / acc[3]);
+    return KBC_OK;
 }
 
 int kbc_adjoint(kbc_handle h, const double* rho0, const double* u0, int nsteps, int ckpt_every,
@@ -1239,49 +1303,58 @@ int kbc_diagnostics_ext(kbc_handle h, double* out)
     return wait_stream(h, 0);
 }
 
-// Rows of the halo of one face: the first of the three populations and the
-// row (relative to interior row 0) in the current field.
-static void halo_rows(const kbc_ctx* h, int face, bool ghost, int* pop0, long long* row)
+// Rows of the halo of one face: the first of its populations and the row
+// (relative to interior row 0) in the current field.  A full halo is all
+// nine populations of the row.
+static void halo_rows(const kbc_ctx* h, int face, bool ghost, bool full, int* pop0, long long* row)
 {
     if (!ghost) {
         // outgoing: the bottom row's b = -1 populations, the top row's b = +1
-        *pop0 = face == 0 ? 0 : 6;
+        *pop0 = full ? 0 : (face == 0 ? 0 : 6);
         *row = face == 0 ? 0 : h->ny - 1;
     } else {
         // incoming: the lower ghost row's b = +1 populations, the upper's b = -1
-        *pop0 = face == 0 ? 6 : 0;
+        *pop0 = full ? 0 : (face == 0 ? 6 : 0);
         *row = face == 0 ? -1 : h->ny;
     }
 }
 
-static int halo_copy(kbc_handle h, int face, void* out, const void* in)
+static int halo_copy(kbc_handle h, int face, int full, void* out, const void* in)
 {
     int rc = check_h(h);
     if (rc) return rc;
     if (!h->slab) return fail(h, KBC_ERR_ARG, "halo exchange needs a y-slab handle (kbc_create_slab)");
     if (face != 0 && face != 1) return fail(h, KBC_ERR_ARG, "face must be 0 (lower) or 1 (upper)");
+    if (full != 0 && full != 1) return fail(h, KBC_ERR_ARG, "full must be 0 or 1");
     if (!(out ? (const void*)out : in)) return fail(h, KBC_ERR_ARG, "NULL buffer");
     if (out && !h->initialized) return fail(h, KBC_ERR_STATE, "field not initialised");
     int pop0;
     long long row;
-    halo_rows(h, face, in != nullptr, &pop0, &row);
+    halo_rows(h, face, in != nullptr, full != 0, &pop0, &row);
     char* field = static_cast<char*>(h->buf[h->cur]) + ((long long)pop0 * h->plane + row * h->nx) * (long long)h->elem;
     const size_t width = (size_t)h->nx * h->elem, pitch = (size_t)h->plane * h->elem;
-    cudaError_t e = out ? cudaMemcpy2DAsync(out, width, field, pitch, width, 3, cudaMemcpyDefault, h->stream)
-                        : cudaMemcpy2DAsync(field, pitch, in, width, width, 3, cudaMemcpyDefault, h->stream);
+    const size_t rows = full ? 9 : 3;
+    cudaError_t e = out ? cudaMemcpy2DAsync(out, width, field, pitch, width, rows, cudaMemcpyDefault, h->stream)
+                        : cudaMemcpy2DAsync(field, pitch, in, width, width, rows, cudaMemcpyDefault, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "halo copy");
     const bool host = !is_device_ptr(out ? (const void*)out : in);
     return host ? wait_stream(h, 0) : KBC_OK;
 }
 
-int kbc_halo_send(kbc_handle h, int face, void* buf) { return halo_copy(h, face, buf, nullptr); }
-
-int kbc_halo_recv(kbc_handle h, int face, const void* buf) { return halo_copy(h, face, nullptr, buf); }
-
-int kbc_halo_bytes(kbc_handle h, size_t* bytes)
+int kbc_halo_send(kbc_handle h, int face, int full, void* buf)
 {
-    if (!h || !bytes) return KBC_ERR_ARG;
-    *bytes = (size_t)3 * h->nx * h->elem;
+    return halo_copy(h, face, full, buf, nullptr);
+}
+
+int kbc_halo_recv(kbc_handle h, int face, int full, const void* buf)
+{
+    return halo_copy(h, face, full, nullptr, buf);
+}
+
+int kbc_halo_bytes(kbc_handle h, int full, size_t* bytes)
+{
+    if (!h || !bytes || (full != 0 && full != 1)) return KBC_ERR_ARG;
+    *bytes = (size_t)(full ? 9 : 3) * h->nx * h->elem;
     return KBC_OK;
 }
 

@@ -561,7 +561,14 @@ diag_partial(const typename C::S* __restrict__ src, double* __restrict__ part, S
         __syncthreads();  // the previous tile's readers are done with the arrays
         for (int q = threadIdx.x; q < HH * HW; q += blockDim.x) {
             const int qy = q / HW, qx = q - qy * HW;
-            const int gx = wrap_mod(x0 + qx - 1, a.nx), gy = wrap_mod(y0 + qy - 1, a.ny);
+            const int gx = wrap_mod(x0 + qx - 1, a.nx);
+            int gy = y0 + qy - 1;
+            if (a.ywrap) {
+                gy = wrap_mod(gy, a.ny);
+            } else if (gy > a.ny) {  // y-slab: rows -1 and ny are ghost rows; beyond, unused
+                sr[qy][qx] = sux[qy][qx] = suy[qy][qx] = 0.0;
+                continue;
+            }
             node_macro<C>(src, (long long)gy * a.nx + gx, a, sr[qy][qx], sux[qy][qx], suy[qy][qx]);
         }
         __syncthreads();
@@ -586,7 +593,7 @@ diag_partial(const typename C::S* __restrict__ src, double* __restrict__ part, S
                 const int ai = i % 3 - 1, bi = i / 3 - 1;
                 int sx = x - ai, sy = y - bi;
                 sx = sx < 0 ? sx + a.nx : (sx >= a.nx ? sx - a.nx : sx);
-                sy = sy < 0 ? sy + a.ny : (sy >= a.ny ? sy - a.ny : sy);
+                sy = pull_row(sy, a);
                 f[i] = C::to_f64(src[(long long)i * a.plane + (long long)sy * a.nx + sx], i, a.cs);
             }
             double rr;
@@ -691,8 +698,9 @@ diag_ext_partial(const typename C::S* __restrict__ src, double* __restrict__ par
 __global__ void diag_ext_final(const double* __restrict__ part, int nblocks,
                                double* __restrict__ out, long long total);
 
-// Reduces part[nblocks][11] (fixed order) into out[KBC_DIAG_N].
+// Reduces part[nblocks][11] (fixed order) into out[KBC_DIAG_N], or with raw
+// into the merged partial set out[11] (the layout of one block's part).
 __global__ void diag_final(const double* __restrict__ part, int nblocks, double* __restrict__ out,
-                           long long total);
+                           long long total, int raw);
 
 }  // namespace kbc

@@ -163,7 +163,7 @@ inline int diag_blocks(long long total, int num_sms)
 
 template <class C>
 cudaError_t launch_diag(const void* src, double* part, int nblocks, double* out, int variant,
-                        const StepArgs& a, cudaStream_t s)
+                        const StepArgs& a, cudaStream_t s, int raw)
 {
     const typename C::S* p = static_cast<const typename C::S*>(src);
     switch (variant) {
@@ -174,7 +174,7 @@ cudaError_t launch_diag(const void* src, double* part, int nblocks, double* out,
     case kD: diag_partial<kD, C><<<nblocks, kDiagBlock, 0, s>>>(p, part, a); break;
     default: return cudaErrorInvalidValue;
     }
-    diag_final<<<1, kDiagBlock, 0, s>>>(part, nblocks, out, (long long)a.nx * a.ny);
+    diag_final<<<1, kDiagBlock, 0, s>>>(part, nblocks, out, (long long)a.nx * a.ny, raw);
     return cudaGetLastError();
 }
 
@@ -258,7 +258,7 @@ cudaError_t launch_adj_grad_u0(const double* rho0, const double* ux0, const doub
     extern template cudaError_t launch_moments<C>(const void*, double*, double*, double*,     \
                                                   const StepArgs&, cudaStream_t, int);        \
     extern template cudaError_t launch_diag<C>(const void*, double*, int, double*, int,       \
-                                               const StepArgs&, cudaStream_t);                \
+                                               const StepArgs&, cudaStream_t, int);           \
     extern template cudaError_t launch_probe<C>(const void*, const long long*, int, double*,  \
                                                 int*, const StepArgs&, cudaStream_t, int);    \
     extern template cudaError_t launch_diag_ext<C>(const void*, double*, int, double*,        \
@@ -285,7 +285,7 @@ cudaError_t launch_adj_grad_u0(const double* rho0, const double* ux0, const doub
     template cudaError_t launch_moments<C>(const void*, double*, double*, double*,            \
                                            const StepArgs&, cudaStream_t, int);               \
     template cudaError_t launch_diag<C>(const void*, double*, int, double*, int,              \
-                                        const StepArgs&, cudaStream_t);                       \
+                                        const StepArgs&, cudaStream_t, int);                  \
     template cudaError_t launch_probe<C>(const void*, const long long*, int, double*, int*,   \
                                          const StepArgs&, cudaStream_t, int);                 \
     template cudaError_t launch_diag_ext<C>(const void*, double*, int, double*,               \

@@ -110,6 +110,7 @@ extern "C" int kbc_diagnostics_noalloc(int nx, int ny, int variant, double beta,
     a.pd = make_params<double>(beta, 0, 2.0, 0.0);
     a.pf = make_params<float>(beta, 0, 2.0, 0.0);
     a.beta = beta;
+    a.ywrap = 1;
     const int nblocks = (int)((total + kNodesPerBlock - 1) / kNodesPerBlock);
     double* result = scratch + (long long)kMaxBlocks * kDiagParts;
     switch (variant) {
@@ -119,7 +120,7 @@ extern "C" int kbc_diagnostics_noalloc(int nx, int ny, int variant, double beta,
     case kC: diag_partial<kC, CodecF64Plain><<<nblocks, kDiagBlock, 0, s>>>(f, scratch, a); break;
     default: diag_partial<kD, CodecF64Plain><<<nblocks, kDiagBlock, 0, s>>>(f, scratch, a); break;
     }
-    diag_final<<<1, kDiagBlock, 0, s>>>(scratch, nblocks, result, total);
+    diag_final<<<1, kDiagBlock, 0, s>>>(scratch, nblocks, result, total, 0);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(out, result, KBC_DIAG_N * sizeof(double), cudaMemcpyDefault, s);

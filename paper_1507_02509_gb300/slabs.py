@@ -9,11 +9,14 @@ periodically in y.  x stays periodic inside every slab.
 
 The device side is the library's y-slab handle (kbc_create_slab,
 kbc_halo_send, kbc_halo_recv): halos are [3][nx] arrays in the storage
-encoding.  This module holds the host-side bookkeeping around it: the row
-partition, the neighbour ranks, the exchange over torch.distributed (NCCL
-between GPUs, gloo between CPU processes; one process per slab), and a
-group of slabs advanced in one process (several handles on one device).
-No lattice Boltzmann arithmetic happens here.
+encoding, or [9][nx] (full rows) before global diagnostics, which each slab
+computes as a partial set (kbc_diagnostics_partial) and the library
+combines in a fixed order (kbc_diagnostics_merge) -- across ranks after one
+all-gather of the sets.  This module holds the host-side bookkeeping around
+it: the row partition, the neighbour ranks, the exchange over
+torch.distributed (NCCL between GPUs, gloo between CPU processes; one
+process per slab), and a group of slabs advanced in one process (several
+handles on one device).  No lattice Boltzmann arithmetic happens here.
 """
 from __future__ import annotations
 
@@ -67,11 +70,24 @@ def exchange(send_lo, send_hi, recv_lo, recv_hi, rank: int, world: int, group=No
         w.wait()
 
 
-def _halo_buffers(lat, count: int):
+def _halo_buffers(lat, count: int, full: bool = False):
     import torch
 
-    nb = lat.halo_bytes
+    nb = lat.full_halo_bytes if full else lat.halo_bytes
     return [torch.empty(nb, dtype=torch.uint8, device=lat.device) for _ in range(count)]
+
+
+def merge_diagnostics(parts):
+    """The KBC_DIAG_N global diagnostics from partial sets [n][KBC_DIAG_PART_N]
+    (in slab order), combined by the library (kbc_diagnostics_merge)."""
+    import numpy as np
+
+    from . import DIAG_NAMES, capi
+
+    parts = np.ascontiguousarray(np.asarray(parts, dtype=np.float64))
+    out = np.zeros(capi.KBC_DIAG_N)
+    capi.kbc_diagnostics_merge(parts.shape[0], parts, out)
+    return dict(zip(DIAG_NAMES, out.tolist()))
 
 
 class SlabGroup:
@@ -124,6 +140,23 @@ class SlabGroup:
             for s in self.slabs:
                 s.step(1)
         return self
+
+    def diagnostics(self) -> dict:
+        """Global diagnostics of the grid (those of kbc_diagnostics): full
+        halos into every ghost row, one partial set per slab, combined."""
+        from . import capi
+
+        world = len(self.slabs)
+        full = [_halo_buffers(s, 2, full=True) for s in self.slabs]
+        for k, s in enumerate(self.slabs):
+            s._bind_stream()
+            capi.kbc_halo_send(s.h, 0, full[k][0], 1)
+            capi.kbc_halo_send(s.h, 1, full[k][1], 1)
+        for k, s in enumerate(self.slabs):
+            lower, upper = neighbours(k, world)
+            capi.kbc_halo_recv(s.h, 0, full[lower][1], 1)
+            capi.kbc_halo_recv(s.h, 1, full[upper][0], 1)
+        return merge_diagnostics([s.diagnostics_partial() for s in self.slabs])
 
     def populations(self):
         """f[9][ny][nx] of the whole grid (float64 CUDA tensor)."""
@@ -179,3 +212,36 @@ class DistributedSlab:
             capi.kbc_halo_recv(self.lat.h, 1, self.recv_hi)
             self.lat.step(1)
         return self
+
+    def diagnostics(self) -> dict:
+        """Global diagnostics of the split grid on every rank: full halos
+        exchanged with the neighbours, this slab's partial set, an all-gather
+        of the sets over the group and the library's merge in rank order."""
+        import numpy as np
+        import torch
+
+        from . import capi
+
+        lo, hi, rlo, rhi = _halo_buffers(self.lat, 4, full=True)
+        self.lat._bind_stream()
+        capi.kbc_halo_send(self.lat.h, 0, lo, 1)
+        capi.kbc_halo_send(self.lat.h, 1, hi, 1)
+        exchange(lo, hi, rlo, rhi, self.rank, self.world, self.group)
+        capi.kbc_halo_recv(self.lat.h, 0, rlo, 1)
+        capi.kbc_halo_recv(self.lat.h, 1, rhi, 1)
+        part = torch.as_tensor(self.lat.diagnostics_partial(), device=self.lat.device)
+        parts = gather_parts(part, self.rank, self.world, self.group)
+        return merge_diagnostics(np.stack([p.cpu().numpy() for p in parts]))
+
+
+def gather_parts(part, rank: int, world: int, group=None):
+    """Every rank's partial diagnostics set, in rank order (an all-gather over
+    the group; a single rank keeps its own)."""
+    if world == 1:
+        return [part]
+    import torch
+    import torch.distributed as dist
+
+    out = [torch.empty_like(part) for _ in range(world)]
+    dist.all_gather(out, part, group=group)
+    return out

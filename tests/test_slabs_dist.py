@@ -131,3 +131,98 @@ def test_partition_and_neighbours():
     assert slabs.RECV_POPS[0] == slabs.SEND_POPS[1]
     assert slabs.RECV_POPS[1] == slabs.SEND_POPS[0]
     assert sorted(va[i] for i in slabs.SEND_POPS[0]) == [-1, 0, 1]
+
+
+def _node_parts(g, variant, beta, rows):
+    """One partial diagnostics set (the layout of kbc_diagnostics_partial)
+    per row range, computed with numpy from the oracle's per-node values of
+    the whole field: sums, node count, mean and sum of squared deviations of
+    |u|^2/2 and of w^2/2 (w by periodic central differences), gamma sum, min
+    and max of the next step's collision."""
+    import oracle as O
+
+    rho, ux, uy = O.macro(g)
+    ke = 0.5 * (ux * ux + uy * uy)
+    w = 0.5 * (np.roll(uy, -1, 1) - np.roll(uy, 1, 1)) - 0.5 * (np.roll(ux, -1, 0) - np.roll(ux, 1, 0))
+    zz = 0.5 * w * w
+    _, gam = O.step(g, variant, beta, 1, want_gamma=True)
+    parts = []
+    for y0, r in rows:
+        sl = slice(y0, y0 + r)
+        k, z, gm = ke[sl].ravel(), zz[sl].ravel(), gam[sl].ravel()
+        parts.append([rho[sl].sum(), (rho * ux)[sl].sum(), (rho * uy)[sl].sum(), k.size,
+                      k.mean(), ((k - k.mean()) ** 2).sum(), z.mean(), ((z - z.mean()) ** 2).sum(),
+                      gm.sum(), gm.min(), gm.max()])
+    return np.array(parts)
+
+
+def _diag_worker(rank, world, port, q, args):
+    os.environ.update({"MASTER_ADDR": "127.0.0.1", "MASTER_PORT": str(port)})
+    import torch.distributed as dist
+
+    from paper_1507_02509_gb300 import slabs
+
+    nx, ny, variant, beta, seed = args
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        rows = slabs.partition(ny, world)
+        mine = _node_parts(_initial(nx, ny, seed), variant, beta, rows)[rank]
+        parts = slabs.gather_parts(torch.tensor(mine), rank, world)
+        d = slabs.merge_diagnostics(np.stack([p.numpy() for p in parts]))
+        q.put((rank, [d[k] for k in sorted(d)], sorted(d)))
+    finally:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def test_slab_ranks_merge_global_diagnostics():
+    """Each gloo rank holds the partial diagnostics of its slab; after one
+    all-gather every rank merges them (kbc_diagnostics_merge, a host routine
+    of the library) into the oracle's diagnostics of the whole field."""
+    import oracle as O
+
+    nx, ny, variant, beta, seed, world = 40, 33, O.B, 0.94, 9, 3
+    port = _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_diag_worker, args=(r, world, port, q, (nx, ny, variant, beta, seed)))
+             for r in range(world)]
+    for p in procs:
+        p.start()
+    got = [q.get(timeout=180) for _ in range(world)]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    ref = O.diagnostics(_initial(nx, ny, seed), variant, beta)
+    names = got[0][2]
+    want = dict(zip(O.DIAG_NAMES, ref))
+    for _, vals, _ in got:
+        assert vals == got[0][1]  # every rank merges the same sets in the same order
+        for name, v in zip(names, vals):
+            assert v == pytest.approx(want[name], rel=1e-12, abs=1e-15), name
+
+
+def test_merge_combines_partial_sets_in_order():
+    """kbc_diagnostics_merge against the direct mean / std / min / max of the
+    concatenated samples, for uneven splits including a single node."""
+    from paper_1507_02509_gb300 import capi
+
+    capi.load()
+    rng = np.random.default_rng(4)
+    k = 1e-3 + 1e-4 * rng.standard_normal(1000)
+    z = 2e-6 * rng.random(1000)
+    gm = 1.0 + 0.3 * rng.standard_normal(1000)
+    cuts = [0, 1, 250, 251, 700, 1000]
+    parts = []
+    for a, b in zip(cuts[:-1], cuts[1:]):
+        kk, zz, gg = k[a:b], z[a:b], gm[a:b]
+        parts.append([a + 0.5, 2 * a, -a, b - a, kk.mean(), ((kk - kk.mean()) ** 2).sum(),
+                      zz.mean(), ((zz - zz.mean()) ** 2).sum(), gg.sum(), gg.min(), gg.max()])
+    parts = np.ascontiguousarray(parts, dtype=np.float64)
+    out = np.zeros(capi.KBC_DIAG_N)
+    capi.kbc_diagnostics_merge(len(parts), parts, out)
+    want = [parts[:, 0].sum(), parts[:, 1].sum(), parts[:, 2].sum(), k.mean(), z.mean(),
+            gm.mean(), gm.min(), gm.max(), k.std(), z.std()]
+    assert np.allclose(out, want, rtol=1e-13, atol=0)
+    with pytest.raises(capi.KBCError):
+        capi.kbc_diagnostics_merge(0, parts, out)
