@@ -274,9 +274,10 @@ int kbc_diagnostics(kbc_handle h, double* out);
  *   [4] mean and [5] sum of squared deviations of |u|^2/2
  *   [6] mean and [7] sum of squared deviations of w^2/2
  *   [8] sum, [9] min, [10] max of gamma
- * with the definitions of kbc_diagnostics.  On a y-slab handle the ghost
- * rows must hold full halos (kbc_halo_recv with full = 1) of the field's
- * current state: the vorticity of the boundary rows and the gamma of the
+ * with the definitions of kbc_diagnostics.  On a y-slab handle both ghost
+ * rows must hold full halos (kbc_halo_recv with full = 1) received since the
+ * field last changed (kbc_step, kbc_init, kbc_set_populations), else
+ * KBC_ERR_STATE: the vorticity of the boundary rows and the gamma of the
  * next step's collision read them.  Synchronises the handle's stream. */
 int kbc_diagnostics_partial(kbc_handle h, double* out);
 

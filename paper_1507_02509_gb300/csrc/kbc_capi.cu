@@ -123,6 +123,7 @@ struct kbc_ctx {
     // y-slab handle: each plane holds a ghost row below and above the ny
     // interior rows; buf[k] points at interior row 0 of allocation alloc[k]
     bool slab = false;
+    int ghosts_full = 0;  // bit f: face f's ghost row holds a full halo of the current state
     void* alloc[2] = {nullptr, nullptr};
     void* buf[2] = {nullptr, nullptr};
     int cur = 0;          // buffer holding the current state
@@ -531,6 +532,7 @@ static int init_common(kbc_handle h, const double* rho, const double* u, bool gr
             rc = init_feq_pipelined(h, rho, u);
             if (rc) return rc;
             h->initialized = true;
+            h->ghosts_full = 0;
             return KBC_OK;
         }
         double* st = static_cast<double*>(h->stage);
@@ -552,6 +554,7 @@ static int init_common(kbc_handle h, const double* rho, const double* u, bool gr
     });
     if (e != cudaSuccess) return cuda_fail(h, e, "init launch");
     h->initialized = true;
+    h->ghosts_full = 0;
     return KBC_OK;
 }
 
@@ -807,6 +810,7 @@ int kbc_set_populations(kbc_handle h, const double* f)
     });
     if (e != cudaSuccess) return cuda_fail(h, e, "set launch");
     h->initialized = true;
+    h->ghosts_full = 0;
     return KBC_OK;
 }
 
@@ -837,6 +841,7 @@ int kbc_step(kbc_handle h, int nsteps)
     if (h->flag_host[0] & 2) return fail(h, KBC_ERR_TIMEOUT, "a device-side wait ran out");
     if (h->flag_host[0]) return fail(h, KBC_ERR_NONFINITE, "non-finite populations detected");
     if (nsteps == 0) return KBC_OK;
+    h->ghosts_full = 0;
     int done = 0;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     const bool capturing = cudaStreamIsCapturing(h->stream, &cs) != cudaSuccess ||
@@ -1015,6 +1020,10 @@ int kbc_diagnostics_partial(kbc_handle h, double* out)
     if (rc) return rc;
     if (!out) return fail(h, KBC_ERR_ARG, "NULL output");
     if (!h->initialized) return fail(h, KBC_ERR_STATE, "field not initialised");
+    if (h->slab && h->ghosts_full != 3)
+        return fail(h, KBC_ERR_STATE,
+                    "a y-slab needs full halos (kbc_halo_recv, full = 1) of the current state in "
+                    "both ghost rows");
     StepArgs a = args_of(h);
     cudaError_t e = by_codec(h->dtype, [&](auto c) {
         using C = decltype(c);
@@ -1174,6 +1183,7 @@ int kbc_adjoint(kbc_handle h, const double* rho0, const double* u0, int nsteps, 
     e = cudaMemcpyAsync(h->buf[h->cur], gN, field, cudaMemcpyDeviceToDevice, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "final state copy");
     h->initialized = true;
+    h->ghosts_full = 0;
     // reverse sweep over segments, recomputing each from its checkpoint
     int lc = 0;
     for (int sgi = nseg - 1; sgi >= 0; --sgi) {
@@ -1337,6 +1347,7 @@ static int halo_copy(kbc_handle h, int face, int full, void* out, const void* in
     cudaError_t e = out ? cudaMemcpy2DAsync(out, width, field, pitch, width, rows, cudaMemcpyDefault, h->stream)
                         : cudaMemcpy2DAsync(field, pitch, in, width, width, rows, cudaMemcpyDefault, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "halo copy");
+    if (in) h->ghosts_full = full ? (h->ghosts_full | (1 << face)) : (h->ghosts_full & ~(1 << face));
     const bool host = !is_device_ptr(out ? (const void*)out : in);
     return host ? wait_stream(h, 0) : KBC_OK;
 }

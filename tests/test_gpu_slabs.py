@@ -182,3 +182,36 @@ def test_slab_group_global_diagnostics(variant, dtype):
         assert got[name] == pytest.approx(want[name], rel=1e-12, abs=1e-15), name
         assert got[name] == pytest.approx(ref[name], rel=1e-11, abs=1e-15), name
         assert alone[name] == pytest.approx(want[name], rel=1e-15, abs=0), name
+
+
+def test_slab_partial_diagnostics_need_current_full_halos():
+    """kbc_diagnostics_partial on a slab refuses (KBC_ERR_STATE) until both
+    ghost rows hold full halos of the current state; a step or a 3-population
+    halo makes them stale again."""
+    nx, ny = 128, 6
+    lat = Lattice(nx, ny, variant="B", beta=0.9, dtype="f32", slab=True)
+    lat.set_populations(representable(random_field(nx, ny, 5), "f32"))
+    full = torch.empty(lat.full_halo_bytes, dtype=torch.uint8, device="cuda")
+    part = torch.empty(lat.halo_bytes, dtype=torch.uint8, device="cuda")
+
+    def refused():
+        with pytest.raises(KBCError) as e:
+            lat.diagnostics_partial()
+        return e.value.status == capi.KBC_ERR_STATE
+
+    assert refused()
+    capi.kbc_halo_send(lat.h, 0, full, 1)
+    capi.kbc_halo_recv(lat.h, 1, full, 1)
+    assert refused()  # one face only
+    capi.kbc_halo_send(lat.h, 1, full, 1)
+    capi.kbc_halo_recv(lat.h, 0, full, 1)
+    assert lat.diagnostics_partial()[3] == nx * ny
+    capi.kbc_halo_send(lat.h, 1, part)
+    capi.kbc_halo_recv(lat.h, 0, part)
+    assert refused()
+    for face in (0, 1):
+        capi.kbc_halo_send(lat.h, 1 - face, full, 1)
+        capi.kbc_halo_recv(lat.h, face, full, 1)
+    lat.step(1)
+    assert refused()
+    lat.close()
