@@ -284,9 +284,9 @@ int kbc_diagnostics_partial(kbc_handle h, double* out);
 /* Combines n >= 1 partial sets parts[n][KBC_DIAG_PART_N] (in that order:
  * sums added, means and sums of squared deviations by Chan, Golub and
  * LeVeque's pairwise formula, minimum and maximum) into the KBC_DIAG_N
- * values of kbc_diagnostics.  Host arithmetic only: no device, no handle.
- * KBC_ERR_ARG for n < 1, NULL pointers or no nodes (message:
- * kbc_last_error(NULL)). */
+ * values of kbc_diagnostics.  Host arithmetic only: no device, no handle;
+ * parts and out are host memory.  KBC_ERR_ARG for n < 1, NULL pointers,
+ * device pointers or no nodes (message: kbc_last_error(NULL)). */
 int kbc_diagnostics_merge(int n, const double* parts, double* out);
 
 /* Further diagnostics of the paper's turbulence figures (FP64 device

@@ -1040,6 +1040,14 @@ int kbc_diagnostics_partial(kbc_handle h, double* out)
 int kbc_diagnostics_merge(int n, const double* parts, double* out)
 {
     if (n < 1 || !parts || !out) return fail(nullptr, KBC_ERR_ARG, "merge: bad argument");
+    // host arithmetic: device pointers are refused (where the runtime can
+    // tell; without a device every pointer is host memory)
+    for (const void* q : {static_cast<const void*>(parts), static_cast<const void*>(out)}) {
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, q) == cudaSuccess && at.type == cudaMemoryTypeDevice)
+            return fail(nullptr, KBC_ERR_ARG, "merge: parts and out must be host memory");
+        cudaGetLastError();
+    }
     // Chan, Golub and LeVeque's pairwise combination of the (count, mean,
     // M2) sets, the sums added, min and max taken, in the order given
     double acc[KBC_DIAG_PART_N];
