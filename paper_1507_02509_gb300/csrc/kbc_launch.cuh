@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include "kbc_adjoint.cuh"
+#include "kbc_adjoint_async.cuh"
 #include "kbc_kernels.cuh"
 #include "kbc_tma.cuh"
 
@@ -191,6 +192,19 @@ cudaError_t launch_diag_ext(const void* src, double* part, int nblocks, double* 
 
 inline int adj_blocks(long long total, int num_sms) { return grid_for(total, 256, num_sms, 8); }
 
+// One reverse step: FP32 storage prefetches each thread's operands by
+// asynchronous copies (adj_step_async); the other storages load them node
+// by node (adj_step).
+template <int VAR, class C>
+void launch_adj_step_v(const typename C::S* g, const typename C::T* li, typename C::T* lo,
+                       double* part, unsigned* fixmask, int nblocks, const StepArgs& a, cudaStream_t s)
+{
+    if constexpr (std::is_same<C, CodecF32>::value)
+        adj_step_async<VAR><<<nblocks, kAdjBlock, 0, s>>>(g, li, lo, part, fixmask, a);
+    else
+        adj_step<VAR, C><<<nblocks, kAdjBlock, 0, s>>>(g, li, lo, part, fixmask, a);
+}
+
 template <class C>
 cudaError_t launch_adj_step(int variant, const void* g, const void* lam_in, void* lam_out,
                             double* part, unsigned* fixmask, int nblocks, const StepArgs& a,
@@ -208,10 +222,10 @@ cudaError_t launch_adj_step(int variant, const void* g, const void* lam_in, void
     const long long words = ((long long)a.nx * a.ny + 31) / 32;
     const int fblocks = (int)((words + 255) / 256 < nblocks ? (words + 255) / 256 : nblocks);
     switch (variant) {
-    case kLBGK: adj_step<kLBGK, C><<<nblocks, kAdjBlock, 0, s>>>(gp, li, lo, part, fixmask, a); break;
+    case kLBGK: launch_adj_step_v<kLBGK, C>(gp, li, lo, part, fixmask, nblocks, a, s); break;
 #define KBC_ADJ_CASE(V)                                                                  \
     case V:                                                                              \
-        adj_step<V, C><<<nblocks, kAdjBlock, 0, s>>>(gp, li, lo, part, fixmask, a);     \
+        launch_adj_step_v<V, C>(gp, li, lo, part, fixmask, nblocks, a, s);               \
         if (fix) adj_fixup<V, C><<<fblocks, 256, 0, s>>>(gp, li, lo, part, fixmask, a); \
         break;
     KBC_ADJ_CASE(kA)
