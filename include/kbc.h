@@ -337,7 +337,7 @@ int kbc_spectrum(int n, const double* u, int nbins, double* E, double* Z, void* 
  * Scratch: a file-scope device array of about 1.4 MB that every GPU that
  * loads the library holds until the process exits; it bounds the grid to
  * nx * ny <= 2^28 nodes (e.g. 16384 x 16384); larger grids give
- * KBC_ERR_ARG.  The first call on each device looks up the array's device
+ * KBC_ERR_ARG.  Every failure leaves its message at kbc_last_error(NULL).  The first call on each device looks up the array's device
  * address (cudaGetSymbolAddress) with that device current, and caches it
  * for that device's context (a call after cudaDeviceReset, which ends the
  * context, looks it up again); make that first call before any stream

@@ -249,11 +249,8 @@ def kbc_spectrum(n: int, u, nbins: int, E, Z, stream=None):
 def kbc_diagnostics_noalloc(nx: int, ny: int, variant: int, beta: float, f, out,
                             stream=None):
     """Diagnostics of a caller-owned FP64 device field, no device allocation."""
-    st = load().kbc_diagnostics_noalloc(int(nx), int(ny), int(variant), float(beta), ptr(f),
-                                        ptr(out), stream)
-    if st != KBC_OK:
-        raise KBCError(st, "kbc_diagnostics_noalloc failed")
-    return st
+    return check(None, load().kbc_diagnostics_noalloc(int(nx), int(ny), int(variant), float(beta),
+                                                      ptr(f), ptr(out), stream))
 
 
 def kbc_adjoint(h, rho0, u0, nsteps: int, ckpt_every: int, objective: int, u_target,

@@ -106,6 +106,14 @@ std::string g_create_error;
 
 }  // namespace
 
+// The message kbc_last_error(NULL) returns, for the calls that have no
+// handle (declared in kbc_launch.cuh).
+int kbc::handle_free_error(int code, const char* msg)
+{
+    g_create_error = msg;
+    return code;
+}
+
 // Row chunks of the host <-> device pipelines of kbc_init and kbc_moments;
 // staging below kPipeMinBytes uses one copy and one kernel.
 constexpr int kPipeChunks = 8;

@@ -26,6 +26,10 @@ struct Launch {
     int num_sms;
 };
 
+// Records msg as the message of kbc_last_error(NULL) and returns code (for
+// the entry points that take no handle).
+int handle_free_error(int code, const char* msg);
+
 constexpr int kRowBlock = 64;
 constexpr int kNodeBlock = 256;
 

@@ -70,22 +70,30 @@ using namespace kbc;
 extern "C" int kbc_diagnostics_noalloc(int nx, int ny, int variant, double beta, const double* f,
                                        double* out, void* stream)
 {
-    if (nx < 1 || ny < 1) return KBC_ERR_ARG;
+    if (nx < 1 || ny < 1) return handle_free_error(KBC_ERR_ARG, "noalloc diagnostics: nx, ny >= 1");
     const long long total = (long long)nx * ny;
-    if (total > kNodesPerBlock * kMaxBlocks) return KBC_ERR_ARG;  // more than 2^28 nodes
+    if (total > kNodesPerBlock * kMaxBlocks)
+        return handle_free_error(KBC_ERR_ARG,
+                                 "noalloc diagnostics: more than 2^28 nodes, the size its static "
+                                 "scratch holds (use kbc_diagnostics)");
     if (variant < KBC_LBGK || variant > KBC_D || !(beta > 0.0 && beta <= 1.0) || !f || !out)
-        return KBC_ERR_ARG;
+        return handle_free_error(KBC_ERR_ARG, "noalloc diagnostics: bad variant, beta or pointer");
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, f) != cudaSuccess) {
         cudaGetLastError();
-        return KBC_ERR_ARG;
+        return handle_free_error(KBC_ERR_ARG, "noalloc diagnostics: f is not a known pointer");
     }
-    if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) return KBC_ERR_ARG;
+    if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+        return handle_free_error(KBC_ERR_ARG,
+                                 "noalloc diagnostics: f must be device memory (staging a host "
+                                 "field would allocate)");
 
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return KBC_ERR_CUDA;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+        return handle_free_error(KBC_ERR_CUDA, "noalloc diagnostics: no usable current device");
     // the kernels read f directly: it must live on the current device
-    if (at.type == cudaMemoryTypeDevice && at.device != dev) return KBC_ERR_ARG;
+    if (at.type == cudaMemoryTypeDevice && at.device != dev)
+        return handle_free_error(KBC_ERR_ARG, "noalloc diagnostics: f is on another device");
     double* scratch = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_mu);
@@ -94,7 +102,7 @@ extern "C" int kbc_diagnostics_noalloc(int nx, int ny, int variant, double beta,
             void* p = nullptr;
             if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
                 cudaGetLastError();
-                return KBC_ERR_CUDA;
+                return handle_free_error(KBC_ERR_CUDA, "noalloc diagnostics: cudaGetSymbolAddress failed");
             }
             g_scratch_addr[dev] = static_cast<double*>(p);
             g_scratch_ctx[dev] = ctx;
@@ -124,14 +132,15 @@ extern "C" int kbc_diagnostics_noalloc(int nx, int ny, int variant, double beta,
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(out, result, KBC_DIAG_N * sizeof(double), cudaMemcpyDefault, s);
-    if (e != cudaSuccess) return KBC_ERR_CUDA;
+    if (e != cudaSuccess) return handle_free_error(KBC_ERR_CUDA, "noalloc diagnostics: launch or copy failed");
     // bounded wait for the result (the shared scratch is free again afterwards)
     const auto t0 = std::chrono::steady_clock::now();
     for (;;) {
         e = cudaStreamQuery(s);
         if (e == cudaSuccess) return KBC_OK;
-        if (e != cudaErrorNotReady) return KBC_ERR_CUDA;
-        if (std::chrono::steady_clock::now() - t0 > std::chrono::seconds(600)) return KBC_ERR_TIMEOUT;
+        if (e != cudaErrorNotReady) return handle_free_error(KBC_ERR_CUDA, "noalloc diagnostics: stream error");
+        if (std::chrono::steady_clock::now() - t0 > std::chrono::seconds(600))
+            return handle_free_error(KBC_ERR_TIMEOUT, "noalloc diagnostics: timed out waiting for the stream");
         std::this_thread::sleep_for(std::chrono::microseconds(20));
     }
 }

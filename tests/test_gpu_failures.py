@@ -63,7 +63,10 @@ def test_bounded_host_wait_times_out_and_recovers():
 
 
 def test_library_memory_comes_from_the_torch_caching_allocator():
+    import gc
+
     use_torch_allocator()
+    gc.collect()  # tensors of earlier tests left in reference cycles are freed now, not mid-test
     torch.cuda.synchronize()
     before = torch.cuda.memory_allocated()
     lat = Lattice(1024, 512, variant="B", beta=0.95, dtype="f32")
