@@ -145,11 +145,11 @@ def kbc_create_slab(nx: int, ny: int, variant: int, beta: float, dtype: int):
     return h
 
 
-def kbc_halo_send(h, face: int, buf, full: int = 0):
+def kbc_halo_send(h, face: int, full: int, buf):
     return check(h, load().kbc_halo_send(h, int(face), int(full), ptr(buf)))
 
 
-def kbc_halo_recv(h, face: int, buf, full: int = 0):
+def kbc_halo_recv(h, face: int, full: int, buf):
     return check(h, load().kbc_halo_recv(h, int(face), int(full), ptr(buf)))
 
 

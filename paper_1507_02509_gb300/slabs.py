@@ -127,12 +127,12 @@ class SlabGroup:
         world = len(self.slabs)
         for k, s in enumerate(self.slabs):
             s._bind_stream()
-            capi.kbc_halo_send(s.h, 0, self._send[k][0])
-            capi.kbc_halo_send(s.h, 1, self._send[k][1])
+            capi.kbc_halo_send(s.h, 0, 0, self._send[k][0])
+            capi.kbc_halo_send(s.h, 1, 0, self._send[k][1])
         for k, s in enumerate(self.slabs):
             lower, upper = neighbours(k, world)
-            capi.kbc_halo_recv(s.h, 0, self._send[lower][1])
-            capi.kbc_halo_recv(s.h, 1, self._send[upper][0])
+            capi.kbc_halo_recv(s.h, 0, 0, self._send[lower][1])
+            capi.kbc_halo_recv(s.h, 1, 0, self._send[upper][0])
 
     def step(self, n: int = 1):
         for _ in range(int(n)):
@@ -150,12 +150,12 @@ class SlabGroup:
         full = [_halo_buffers(s, 2, full=True) for s in self.slabs]
         for k, s in enumerate(self.slabs):
             s._bind_stream()
-            capi.kbc_halo_send(s.h, 0, full[k][0], 1)
-            capi.kbc_halo_send(s.h, 1, full[k][1], 1)
+            capi.kbc_halo_send(s.h, 0, 1, full[k][0])
+            capi.kbc_halo_send(s.h, 1, 1, full[k][1])
         for k, s in enumerate(self.slabs):
             lower, upper = neighbours(k, world)
-            capi.kbc_halo_recv(s.h, 0, full[lower][1], 1)
-            capi.kbc_halo_recv(s.h, 1, full[upper][0], 1)
+            capi.kbc_halo_recv(s.h, 0, 1, full[lower][1])
+            capi.kbc_halo_recv(s.h, 1, 1, full[upper][0])
         return merge_diagnostics([s.diagnostics_partial() for s in self.slabs])
 
     def populations(self):
@@ -204,12 +204,12 @@ class DistributedSlab:
 
         for _ in range(int(n)):
             self.lat._bind_stream()
-            capi.kbc_halo_send(self.lat.h, 0, self.send_lo)
-            capi.kbc_halo_send(self.lat.h, 1, self.send_hi)
+            capi.kbc_halo_send(self.lat.h, 0, 0, self.send_lo)
+            capi.kbc_halo_send(self.lat.h, 1, 0, self.send_hi)
             exchange(self.send_lo, self.send_hi, self.recv_lo, self.recv_hi, self.rank,
                      self.world, self.group)
-            capi.kbc_halo_recv(self.lat.h, 0, self.recv_lo)
-            capi.kbc_halo_recv(self.lat.h, 1, self.recv_hi)
+            capi.kbc_halo_recv(self.lat.h, 0, 0, self.recv_lo)
+            capi.kbc_halo_recv(self.lat.h, 1, 0, self.recv_hi)
             self.lat.step(1)
         return self
 
@@ -224,11 +224,11 @@ class DistributedSlab:
 
         lo, hi, rlo, rhi = _halo_buffers(self.lat, 4, full=True)
         self.lat._bind_stream()
-        capi.kbc_halo_send(self.lat.h, 0, lo, 1)
-        capi.kbc_halo_send(self.lat.h, 1, hi, 1)
+        capi.kbc_halo_send(self.lat.h, 0, 1, lo)
+        capi.kbc_halo_send(self.lat.h, 1, 1, hi)
         exchange(lo, hi, rlo, rhi, self.rank, self.world, self.group)
-        capi.kbc_halo_recv(self.lat.h, 0, rlo, 1)
-        capi.kbc_halo_recv(self.lat.h, 1, rhi, 1)
+        capi.kbc_halo_recv(self.lat.h, 0, 1, rlo)
+        capi.kbc_halo_recv(self.lat.h, 1, 1, rhi)
         part = torch.as_tensor(self.lat.diagnostics_partial(), device=self.lat.device)
         parts = gather_parts(part, self.rank, self.world, self.group)
         return merge_diagnostics(np.stack([p.cpu().numpy() for p in parts]))

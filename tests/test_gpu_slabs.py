@@ -43,17 +43,17 @@ def test_halo_format(dtype):
     npd = np.float64 if dtype == "f64" else np.float32
     for face, row in ((0, 0), (1, ny - 1)):
         buf = np.zeros(nb, dtype=np.uint8)
-        capi.kbc_halo_send(lat.h, face, buf)
+        capi.kbc_halo_send(lat.h, face, 0, buf)
         pops = list(slabs.SEND_POPS[face])
         got = buf.view(npd).reshape(3, nx).astype(np.float64) + W[pops][:, None]
         assert np.array_equal(got, g[pops, row]), face
     # a single slab fed its own halos is the periodic grid
     lo = torch.empty(nb, dtype=torch.uint8, device="cuda")
     hi = torch.empty_like(lo)
-    capi.kbc_halo_send(lat.h, 0, lo)
-    capi.kbc_halo_send(lat.h, 1, hi)
-    capi.kbc_halo_recv(lat.h, 0, hi)
-    capi.kbc_halo_recv(lat.h, 1, lo)
+    capi.kbc_halo_send(lat.h, 0, 0, lo)
+    capi.kbc_halo_send(lat.h, 1, 0, hi)
+    capi.kbc_halo_recv(lat.h, 0, 0, hi)
+    capi.kbc_halo_recv(lat.h, 1, 0, lo)
     lat.step(1)
     got = lat.populations().cpu().numpy()
     lat.close()
@@ -140,7 +140,7 @@ def test_slab_refusals():
     lat.init(np.ones((8, 128)), np.zeros((8, 128)), np.zeros((8, 128)))
     buf = torch.empty(lat.halo_bytes, dtype=torch.uint8, device="cuda")
     for call in (lambda: lat.step(2), lambda: lat.diagnostics(), lambda: lat.diagnostics_ext(),
-                 lambda: capi.kbc_halo_send(lat.h, 2, buf),
+                 lambda: capi.kbc_halo_send(lat.h, 2, 0, buf),
                  lambda: lat.init(np.ones((8, 128)), np.zeros((8, 128)), np.zeros((8, 128)),
                                   grad=True)):
         with pytest.raises(KBCError) as e:
@@ -151,7 +151,7 @@ def test_slab_refusals():
     lat.close()
     plain = Lattice(128, 8, variant="B", beta=0.9, dtype="f32")
     with pytest.raises(KBCError) as e:
-        capi.kbc_halo_send(plain.h, 0, buf)
+        capi.kbc_halo_send(plain.h, 0, 0, buf)
     assert e.value.status == capi.KBC_ERR_ARG
     plain.close()
 
@@ -200,18 +200,18 @@ def test_slab_partial_diagnostics_need_current_full_halos():
         return e.value.status == capi.KBC_ERR_STATE
 
     assert refused()
-    capi.kbc_halo_send(lat.h, 0, full, 1)
-    capi.kbc_halo_recv(lat.h, 1, full, 1)
+    capi.kbc_halo_send(lat.h, 0, 1, full)
+    capi.kbc_halo_recv(lat.h, 1, 1, full)
     assert refused()  # one face only
-    capi.kbc_halo_send(lat.h, 1, full, 1)
-    capi.kbc_halo_recv(lat.h, 0, full, 1)
+    capi.kbc_halo_send(lat.h, 1, 1, full)
+    capi.kbc_halo_recv(lat.h, 0, 1, full)
     assert lat.diagnostics_partial()[3] == nx * ny
-    capi.kbc_halo_send(lat.h, 1, part)
-    capi.kbc_halo_recv(lat.h, 0, part)
+    capi.kbc_halo_send(lat.h, 1, 0, part)
+    capi.kbc_halo_recv(lat.h, 0, 0, part)
     assert refused()
     for face in (0, 1):
-        capi.kbc_halo_send(lat.h, 1 - face, full, 1)
-        capi.kbc_halo_recv(lat.h, face, full, 1)
+        capi.kbc_halo_send(lat.h, 1 - face, 1, full)
+        capi.kbc_halo_recv(lat.h, face, 1, full)
     lat.step(1)
     assert refused()
     lat.close()
