@@ -373,7 +373,11 @@ __global__ void init_grad(const double* __restrict__ rho, const double* __restri
                           StepArgs a)
 {
     const long long total = (long long)a.nx * a.ny;
+    // cs^2 = 1/3: the divisions by cs^2 and 2 cs^4 of Eq. Grad are the
+    // multiplications by 3 and 4.5 (double division is many FP64-pipe
+    // instructions, and this kernel is bound by that pipe)
     const double cs2 = 1.0 / 3.0;
+    const double half_inv_beta = 0.5 / a.beta;
     for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < total;
          n += (long long)gridDim.x * blockDim.x) {
         const int y = (int)(n / a.nx), x = (int)(n - (long long)y * a.nx);
@@ -386,7 +390,7 @@ __global__ void init_grad(const double* __restrict__ rho, const double* __restri
         const double dxux = 0.5 * (ux[xp] - ux[xm]), dxuy = 0.5 * (uy[xp] - uy[xm]);
         const double dyux = 0.5 * (ux[yp] - ux[ym]), dyuy = 0.5 * (uy[yp] - uy[ym]);
         const double r = rho[n], u0 = ux[n], u1 = uy[n];
-        const double c = r * cs2 / (2.0 * a.beta);
+        const double c = r * cs2 * half_inv_beta;
         // non-equilibrium-shifted stress minus the isotropic part rho cs2 delta
         const double sxx = r * u0 * u0 - c * 2.0 * dxux;
         const double syy = r * u1 * u1 - c * 2.0 * dyuy;
@@ -394,9 +398,9 @@ __global__ void init_grad(const double* __restrict__ rho, const double* __restri
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             const double vx = va(i), vy = vb(i);
-            const double lin = r * (u0 * vx + u1 * vy) / cs2;
+            const double lin = 3.0 * r * (u0 * vx + u1 * vy);
             const double quad = sxx * (vx * vx - cs2) + syy * (vy * vy - cs2) + 2.0 * sxy * vx * vy;
-            const double fi = wgt(i) * (r + lin + quad / (2.0 * cs2 * cs2));
+            const double fi = wgt(i) * (r + lin + 4.5 * quad);
             dst[(long long)i * a.plane + n] = C::from_f64(fi - wgt(i), i, a.cs);
         }
     }
@@ -458,8 +462,9 @@ __device__ __forceinline__ void node_macro(const typename C::S* __restrict__ src
     const double jx = ((d[2] - d[0]) + (d[8] - d[6])) + (d[5] - d[3]);
     const double jy = ((d[6] - d[0]) + (d[8] - d[2])) + (d[7] - d[1]);
     rho = 1.0 + drho;
-    ux = jx / rho;
-    uy = jy / rho;
+    const double irho = 1.0 / rho;  // one division for both components
+    ux = jx * irho;
+    uy = jy * irho;
 }
 
 template <class C>
