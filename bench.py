@@ -463,6 +463,8 @@ def run_ours(args):
         torch.cuda.empty_cache()
         extras["adjoint"] = adjoint_extras(args, local)
         torch.cuda.empty_cache()
+        extras["next_rows"] = next_rows_extras(args, rho, ux, uy, beta, peak, stream)
+        torch.cuda.empty_cache()
         # the FP64 storage path is bound by the FP64 pipe: its ceiling is the
         # measured DFMA issue rate, its use the FP64 thread-instructions per
         # node (ncu, profiles/) at the measured update rate
@@ -557,6 +559,90 @@ def adjoint_extras(args, local):
     res["what"] = ("kbc_adjoint: forward with checkpoints + reverse sweep with segment recompute; "
                    "2000 steps timed as the configuration asks, but its gradient is "
                    "rounding-dominated beyond valid_steps")
+    return res
+
+
+def next_rows_extras(args, rho, ux, uy, beta, peak, stream):
+    """The further rows of the path on the bench field (F32 storage, KBC B):
+    Grad initialisation against the equilibrium one, the regularised
+    stabiliser gamma = 1/beta (the step kernel of gamma*), the exact
+    stabiliser (the per-node all-double kernel with the Newton root), the
+    extended diagnostics, the spectra, and the y-slab split of the grid into
+    four slabs on this GPU (halo exchange before every step).  Times from
+    CUDA events on the bound stream (host-returning calls: wall clock around
+    the call)."""
+    import numpy as np
+    import torch
+
+    from paper_1507_02509_gb300 import Lattice, capi, slabs, spectra
+
+    n = args.n
+    nodes = n * n
+    res = {}
+
+    def events(fn, reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        fn()  # warm-up
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        b.synchronize()
+        return a.elapsed_time(b) / 1e3 / reps
+
+    u = torch.stack((ux, uy)).contiguous()
+    lat = Lattice(n, n, variant="B", beta=beta, dtype="f32")
+    for name, fn in (("init_feq", lambda: capi.kbc_init(lat.h, rho, u)),
+                     ("init_grad", lambda: capi.kbc_init_grad(lat.h, rho, u))):
+        t = events(fn, 3)
+        gbs = 60.0 * nodes / t / 1e9  # rho, u in (FP64), nine FP32 populations out
+        res[name] = {"ms": round(t * 1e3, 3), "gbs": round(gbs, 1), "frac": round(gbs / peak, 4),
+                     "algorithmic_bytes_per_node": 60}
+    lat.init(rho, ux, uy)
+    lat.set_gamma(1.0 / beta)
+    t = events(lambda: lat.step(100), 1) / 100
+    res["regularised_gamma"] = {"mlups": round(nodes / t / 1e6, 1),
+                                "frac": round(72.0 * nodes / t / 1e9 / peak, 4),
+                                "what": "gamma fixed at 1/beta, F32, the vector-row step kernel"}
+    lat.close()
+    ne = min(n, 4096)
+    le = Lattice(ne, ne, variant="B", beta=beta, dtype="f32")
+    le.init(rho[:ne, :ne].contiguous(), ux[:ne, :ne].contiguous(), uy[:ne, :ne].contiguous())
+    le.set_gamma("exact")
+    t = events(lambda: le.step(5), 1) / 5
+    res["exact_gamma"] = {"n": ne, "mlups": round(ne * ne / t / 1e6, 1),
+                          "frac_hbm": round(72.0 * ne * ne / t / 1e9 / peak, 4),
+                          "what": "root of the exact entropic condition by Newton in FP64 per node "
+                                  "(F32 storage): bound by the FP64 pipe and the per-node kernel"}
+    le.close()
+    lat = Lattice(n, n, variant="B", beta=beta, dtype="f32")
+    lat.init(rho, ux, uy)
+    lat.sync()
+    out = np.zeros(capi.KBC_DIAG_EXT_N)
+    capi.kbc_diagnostics_ext(lat.h, out)
+    t0 = time.perf_counter()
+    for _ in range(2):
+        capi.kbc_diagnostics_ext(lat.h, out)
+    res["diagnostics_ext_ms"] = round((time.perf_counter() - t0) / 2 * 1e3, 3)
+    _, vx, vy = lat.moments()
+    lat.close()
+    spectra.energy_spectrum(vx, vy)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    spectra.energy_spectrum(vx, vy)
+    torch.cuda.synchronize()
+    res["spectrum_ms"] = round((time.perf_counter() - t0) * 1e3, 3)
+    del vx, vy
+    torch.cuda.empty_cache()
+    grp = slabs.SlabGroup(n, n, 4, variant="B", beta=beta, dtype="f32")
+    grp.init(rho, ux, uy)
+    t = events(lambda: grp.step(20), 1) / 20
+    grp.close()
+    res["slabs_4_on_one_gpu"] = {"mlups": round(nodes / t / 1e6, 1),
+                                 "frac": round(72.0 * nodes / t / 1e9 / peak, 4),
+                                 "what": "the grid as four y-slabs with a halo exchange (two "
+                                         "device copies per slab) before every step"}
     return res
 
 
