@@ -213,7 +213,14 @@ __device__ __forceinline__ L collide(L (&d)[9], const CollideParams<typename L::
     if constexpr (U) irho = irho * L(p.unit_c);  // j is in units of c
     const L ux = jx * irho, uy = jy * irho;
     const L uxx = ux * ux, uyy = uy * uy;
-    const L nusq15 = L(-1.5) * (uxx + uyy);
+    // storage units also collide in packed node pairs (Lf2), where a packed
+    // product whose only use is an addition may be fused with it into one
+    // fma: there |u|^2 is formed by an explicit fma, the same operation in
+    // both lane types (elsewhere every product has a second use or scales by
+    // a power of two, exact either way)
+    L nusq15;
+    if constexpr (U) nusq15 = L(-1.5) * fmaL(ux, ux, uyy);
+    else nusq15 = L(-1.5) * (uxx + uyy);
     const L sxy = ux + uy, dxy = ux - uy;
 
     L P[9], df[9];
@@ -426,6 +433,27 @@ __device__ __forceinline__ T collide_node(T (&f)[9], const CollideParams<T>& p, 
     rho = r.v;
     hit = (h & 1u) != 0u;
     return g.v;
+}
+
+// Two nodes in one packed lane pair (float only); the same bits as two
+// collide_node calls.  hits: bit 0 / 1 for node 0 / 1.
+template <int VAR, bool U = false>
+__device__ __forceinline__ void collide_pair(float (&f0)[9], float (&f1)[9],
+                                             const CollideParams<float>& p, float& rho0,
+                                             float& rho1, unsigned& hits)
+{
+    Lf2 d[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) d[i] = Lf2(f0[i], f1[i]);
+    Lf2 r;
+    collide<VAR, Lf2, U>(d, p, r, hits);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        f0[i] = d[i].lo();
+        f1[i] = d[i].hi();
+    }
+    rho0 = r.lo();
+    rho1 = r.hi();
 }
 
 }  // namespace kbc

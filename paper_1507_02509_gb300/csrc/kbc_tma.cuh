@@ -259,7 +259,8 @@ step_tma(const typename C::S* __restrict__ src, typename C::S* __restrict__ dst,
         // this warp's operands are in registers: release the stage
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
-        const unsigned hits = collide_vec<VAR, C::kUnits>(f, p, bad);
+        // storage units (FP16): node pairs in packed FP32x2 arithmetic
+        const unsigned hits = collide_vec<VAR, C::kUnits, C::kUnits>(f, p, bad);
         if constexpr (VAR != kLBGK) {
             if (a.fix_list) record_fix_mask<NV>(hits, y * a.nx + x0 + lx, a);
         }
