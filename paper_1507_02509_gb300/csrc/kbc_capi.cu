@@ -116,7 +116,7 @@ int kbc::handle_free_error(int code, const char* msg)
 
 // Row chunks of the host <-> device pipelines of kbc_init and kbc_moments;
 // staging below kPipeMinBytes uses one copy and one kernel.
-constexpr int kPipeChunks = 8;
+constexpr int kPipeChunks = 32;
 constexpr size_t kPipeMinBytes = (size_t)64 << 20;
 
 struct kbc_ctx {
