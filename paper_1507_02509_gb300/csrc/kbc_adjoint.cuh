@@ -38,6 +38,260 @@ template <int VAR, typename T> constexpr int adj_min_blocks()
     return std::is_same<T, double>::value ? 1 : ((VAR == kC || VAR == kD) ? 5 : 4);
 }
 
+// Single-precision reverse collision in opposite-pair lanes: population
+// pair k = 0..3 holds (i = k, i = 8 - k) in one packed FP32x2 lane (Lf2).
+// The two members have velocities v and -v and the same weight, so every
+// per-population step of the reverse (equilibrium, split, entropic
+// products, their adjoints) is one packed operation for two populations,
+// with sign pairs (a, -a), (b, -b) for the velocity components; the rest
+// population i = 4 and the scalar moments stay scalar.  Same mathematics as
+// the generic collide_adjoint below, in a different rounding order.
+template <int VAR>
+__device__ __forceinline__ bool collide_adjoint_pairs(const float (&d)[9], const float (&lam)[9],
+                                                      const CollideParams<float>& p,
+                                                      float (&mu)[9], float& beta_bar)
+{
+    using L = Lf2;
+    constexpr bool central = (VAR == kA || VAR == kB);
+    bool guarded = false;
+    // ---------------------------------------------------------------- forward
+    // the pairwise moment sums of the generic path
+    const float drho = ((d[0] + d[8]) + (d[2] + d[6])) + ((d[1] + d[7]) + (d[3] + d[5])) + d[4];
+    const float jx = ((d[2] - d[0]) + (d[8] - d[6])) + (d[5] - d[3]);
+    const float jy = ((d[6] - d[0]) + (d[8] - d[2])) + (d[7] - d[1]);
+    const float rho = 1.0f + drho;
+    const float irho = rcp_fast(rho);
+    const float ux = jx * irho, uy = jy * irho;
+    const float usq15 = 1.5f * (ux * ux + uy * uy);
+    const L nusq(-usq15), lrho(rho), ldrho(drho), c3(3.0f), c45(4.5f);
+    // xi of pair k's first member (v_k . u); the second has -xi
+    auto xi_of = [&](int k) {
+        const int a = va(k), b = vb(k);
+        const float x = (a == 0) ? 0.0f : (a > 0 ? ux : -ux);
+        return (b == 0) ? x : (b > 0 ? x + uy : x - uy);
+    };
+    L D[4], LM[4], P[4], DF[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        D[k] = L(d[k], d[8 - k]);
+        LM[k] = L(lam[k], lam[8 - k]);
+        const float x = xi_of(k);
+        const L X(x, -x);
+        P[k] = fmaL(X, fmaL(c45, X, c3), nusq);
+        DF[k] = fmaL(L(-(float)wgt(k)), fmaL(lrho, P[k], ldrho), D[k]);
+    }
+    const float P4 = -usq15;
+    const float df4 = d[4] - (float)wgt(4) * (drho + rho * P4);
+    L DFB[4], PB[4];
+    const L n2b(-p.two_beta);
+    L BB(0.0f);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        DFB[k] = n2b * LM[k];
+        PB[k] = L(0.0f);
+        BB = fmaL(LM[k], DF[k], BB);
+    }
+    float dfb4 = -p.two_beta * lam[4], pb4 = 0.0f;
+    float bb = -2.0f * ((BB.lo() + BB.hi()) + lam[4] * df4);
+    float uxb = 0.0f, uyb = 0.0f;
+    if constexpr (VAR != kLBGK) {
+        const L s02 = DF[0] + DF[2];  // (df0 + df2, df8 + df6)
+        const float corner = s02.lo() + s02.hi();
+        const float m20 = corner + (DF[3].lo() + DF[3].hi());
+        const float m02 = corner + (DF[1].lo() + DF[1].hi());
+        const float m11 = (DF[0].lo() + DF[0].hi()) - (DF[2].lo() + DF[2].hi());
+        float c20, c02;
+        if constexpr (VAR == kA || VAR == kC) {
+            c20 = m20;
+            c02 = m02;
+        } else {
+            c20 = 0.5f * (m20 - m02);
+            c02 = -c20;
+        }
+        // 1-D dual vectors at c (u for the central basis, 0 for the natural):
+        // e0 = (c(c-1)/2, 1 - c^2, c(c+1)/2), e1 = (c - 1/2, -2c, c + 1/2),
+        // e2 = (1/2, -1, 1/2); the outer entries as pairs (in both orders)
+        const float cx = central ? ux : 0.0f, cy = central ? uy : 0.0f;
+        const L lcx(cx), lcy(cy), h(0.5f);
+        const L e0x02 = (h * lcx) * (lcx + L(-1.0f, 1.0f)), e0x20 = (h * lcx) * (lcx + L(1.0f, -1.0f));
+        const L e0y02 = (h * lcy) * (lcy + L(-1.0f, 1.0f));
+        const L e1x02 = lcx + L(-0.5f, 0.5f), e1x20 = lcx + L(0.5f, -0.5f);
+        const L e1y02 = lcy + L(-0.5f, 0.5f), e1y20 = lcy + L(0.5f, -0.5f);
+        const float e0x1 = 1.0f - cx * cx, e0y1 = 1.0f - cy * cy, e1x1 = -2.0f * cx, e1y1 = -2.0f * cy;
+        // ds(a,b) = m11 e1x[a] e1y[b] + (e2[a] c20 e0y[b] + e2[b] c02 e0x[a])
+        const L lm11(m11), lc20(c20), lc02(c02);
+        const L Cx02 = lm11 * e1x02, Cx20 = lm11 * e1x20, Bx02 = lc02 * e0x02, Bx20 = lc02 * e0x20;
+        const L Ay02 = lc20 * e0y02;
+        const float cx1 = m11 * e1x1, bx1 = c02 * e0x1, ay1 = c20 * e0y1;
+        L DS[4];
+        DS[0] = fmaL(Cx02, e1y02, fmaL(h, Ay02, h * Bx02));
+        DS[1] = fmaL(L(cx1), e1y02, fmaL(L(-1.0f), Ay02, L(0.5f * bx1)));
+        DS[2] = fmaL(Cx20, e1y02, fmaL(h, Ay02, h * Bx20));
+        DS[3] = fmaL(Cx02, L(e1y1), fmaL(h, L(ay1), -Bx02));
+        const float ds4 = cx1 * e1y1 - (ay1 + bx1);
+        // entropic weights q_i = 1 / (W_i (1 + P_i)) by Montgomery's
+        // simultaneous inversion over the pairs (one reciprocal)
+        L X1[4], PRE[4], WI[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) X1[k] = L(1.0f) + P[k];
+        const float x4 = 1.0f + P4;
+        PRE[0] = X1[0];
+#pragma unroll
+        for (int k = 1; k < 4; ++k) PRE[k] = PRE[k - 1] * X1[k];
+        const float prod8 = PRE[3].lo() * PRE[3].hi();
+        const float r = rcp_fast(prod8 * x4);
+        const float wi4 = r * prod8;
+        const float rx4 = r * x4;
+        L R(rx4 * PRE[3].hi(), rx4 * PRE[3].lo());  // 1 / PRE[3], per member
+#pragma unroll
+        for (int k = 3; k >= 1; --k) {
+            WI[k] = R * PRE[k - 1];
+            R = R * X1[k];
+        }
+        WI[0] = R;
+        L DH[4], Q[4];
+        L SH(0.0f), HH(0.0f);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            DH[k] = DF[k] - DS[k];
+            Q[k] = L((float)inv_wgt(k)) * WI[k];
+            const L t = DH[k] * Q[k];
+            SH = fmaL(DS[k], t, SH);
+            HH = fmaL(DH[k], t, HH);
+        }
+        const float dh4 = df4 - ds4, q4 = (float)inv_wgt(4) * wi4;
+        const float sh = (SH.lo() + SH.hi()) + ds4 * dh4 * q4;
+        const float hh = (HH.lo() + HH.hi()) + dh4 * dh4 * q4;
+        float ch, Rr = 0.0f;
+        const bool has_h = hh > 0.0f;
+        guarded = !p.fixed && p.guard > 0.0f && !(hh > p.guard);
+        const float ihh = has_h ? rcp_fast(hh) : 0.0f;
+        if (p.fixed) {
+            ch = p.ch_fixed;
+        } else if (has_h) {
+            Rr = sh * ihh;
+            ch = p.one_m_2beta * (1.0f + Rr);
+        } else {
+            ch = 0.0f;
+        }
+        // ---------------------------------------------------------- reverse
+        const L nch(-ch);
+        L DHB[4], DSB[4];
+        L CHB(0.0f);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            DHB[k] = nch * LM[k];
+            CHB = fmaL(LM[k], DH[k], CHB);
+        }
+        float dhb4 = -ch * lam[4];
+        const float chb = -((CHB.lo() + CHB.hi()) + lam[4] * dh4);
+        float Rb = 0.0f;
+        if (p.fixed) {
+            bb += chb * (p.gamma_fixed - 2.0f);
+        } else if (has_h) {
+            bb += chb * (-2.0f * (1.0f + Rr));
+            Rb = chb * p.one_m_2beta;
+        }
+        const float shb = Rb * ihh;
+        const float hhb = -Rb * Rr * ihh;
+        const L lshb(shb), lhhb(hhb), lhhb2(2.0f * hhb);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const L t = DH[k] * Q[k];
+            DSB[k] = lshb * t;
+            DHB[k] = fmaL(lshb, DS[k] * Q[k], fmaL(lhhb2, t, DHB[k]));
+            const L qb = DH[k] * fmaL(lshb, DS[k], lhhb * DH[k]);
+            PB[k] = PB[k] - (qb * (Q[k] * Q[k])) * L((float)wgt(k));  // q_i / x_i = W_i q_i^2
+            DFB[k] = DFB[k] + DHB[k];
+            DSB[k] = DSB[k] - DHB[k];
+        }
+        float dsb4 = shb * dh4 * q4;
+        dhb4 += shb * ds4 * q4 + 2.0f * hhb * dh4 * q4;
+        pb4 -= (shb * ds4 * dh4 + hhb * dh4 * dh4) * (q4 * q4) * (float)wgt(4);
+        dfb4 += dhb4;
+        dsb4 -= dhb4;
+        // reverse of ds through per-axis partial sums of D(a,b) = dsb[3b + a]
+        // (rows b: S, V; columns a: Ta, U), outer entries as pairs
+        const L DSB2s(DSB[2].hi(), DSB[2].lo());  // (dsb6, dsb2)
+        const L S02 = fmaL(h, DSB[0] + DSB[2], -DSB[1]);
+        const float S1 = 0.5f * (DSB[3].lo() + DSB[3].hi()) - dsb4;
+        const L T02 = fmaL(h, DSB[0] + DSB2s, -DSB[3]);
+        const float T1 = 0.5f * (DSB[1].lo() + DSB[1].hi()) - dsb4;
+        const L U02 = fmaL(e1y02, DSB[0], fmaL(L(e1y1), DSB[3], e1y20 * DSB2s));
+        const float U1 = e1y02.lo() * DSB[1].lo() + e1y1 * dsb4 + e1y02.hi() * DSB[1].hi();
+        const L V02 = fmaL(e1x02, DSB[0], fmaL(L(e1x1), DSB[1], e1x20 * DSB[2]));
+        const float V1 = e1x02.lo() * DSB[3].lo() + e1x1 * dsb4 + e1x02.hi() * DSB[3].hi();
+        const L pc20 = e0y02 * S02, pc02 = e0x02 * T02, pm11 = e1x02 * U02;
+        const float c20b = (pc20.lo() + pc20.hi()) + e0y1 * S1;
+        const float c02b = (pc02.lo() + pc02.hi()) + e0x1 * T1;
+        const float m11b = (pm11.lo() + pm11.hi()) + e1x1 * U1;
+        if constexpr (central) {
+            // d e0(c)/dc = e1(c), d e1(c)/dc = (1, -2, 1), with e0xb = c02 Ta,
+            // e1xb = m11 U, e0yb = c20 S, e1yb = m11 V
+            const L tx = e1x02 * T02, ty = e1y02 * S02;
+            uxb += c02 * ((tx.lo() + tx.hi()) + e1x1 * T1) + m11 * ((U02.lo() + U02.hi()) - 2.0f * U1);
+            uyb += c20 * ((ty.lo() + ty.hi()) + e1y1 * S1) + m11 * ((V02.lo() + V02.hi()) - 2.0f * V1);
+        }
+        float m20b, m02b;
+        if constexpr (VAR == kA || VAR == kC) {
+            m20b = c20b;
+            m02b = c02b;
+        } else {
+            m20b = 0.5f * (c20b - c02b);
+            m02b = -m20b;
+        }
+        // df_i += a^2 m20b + b^2 m02b + a b m11b: the same for both members
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int a = va(k), b = vb(k);
+            float inc = 0.0f;
+            if (a != 0) inc = m20b;
+            if (b != 0) inc = (a != 0) ? inc + m02b : m02b;
+            if (a != 0 && b != 0) inc = (a == b) ? inc + m11b : inc - m11b;
+            DFB[k] = DFB[k] + L(inc);
+        }
+    }
+    // ------------------------------------------------- equilibrium and moments
+    L MU[4];
+    L DRHOB(0.0f), USQB(0.0f), UXB(0.0f), UYB(0.0f);
+    const L c9(9.0f);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int a = va(k), b = vb(k);
+        const float x = xi_of(k);
+        const L X(x, -x);
+        const L PR = fmaL(X, fmaL(c45, X, c3), nusq);
+        const L W((float)wgt(k));
+        MU[k] = LM[k] + DFB[k];
+        DRHOB = DRHOB - DFB[k] * fmaL(W, PR, W);
+        PB[k] = PB[k] - DFB[k] * L((float)wgt(k) * rho);
+        USQB = USQB - PB[k];
+        const L XIB = PB[k] * fmaL(c9, X, c3);
+        if (a != 0) UXB = fmaL(L((float)a, (float)-a), XIB, UXB);
+        if (b != 0) UYB = fmaL(L((float)b, (float)-b), XIB, UYB);
+    }
+    mu[4] = lam[4] + dfb4;
+    float drhob = (DRHOB.lo() + DRHOB.hi()) - dfb4 * (float)wgt(4) * (1.0f + P4);
+    pb4 -= dfb4 * (float)wgt(4) * rho;
+    const float usqb = (USQB.lo() + USQB.hi()) - pb4;
+    uxb += (UXB.lo() + UXB.hi()) + 3.0f * ux * usqb;
+    uyb += (UYB.lo() + UYB.hi()) + 3.0f * uy * usqb;
+    const float jxb = uxb * irho, jyb = uyb * irho;
+    const float irhob = uxb * jx + uyb * jy;
+    drhob -= irhob * irho * irho;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int a = va(k), b = vb(k);
+        const float c = (a == 0 ? 0.0f : (a > 0 ? jxb : -jxb)) + (b == 0 ? 0.0f : (b > 0 ? jyb : -jyb));
+        MU[k] = MU[k] + L(drhob + c, drhob - c);
+        mu[k] = MU[k].lo();
+        mu[8 - k] = MU[k].hi();
+    }
+    mu[4] += drhob;
+    beta_bar = bb;
+    return guarded;
+}
+
 // Returns true when the entropic denominator rho <dh|dh> is at or below
 // p.guard (entropic gamma only): there the derivative of gamma* with respect
 // to f, which carries 1 / <dh|dh>, is not resolved in the lane's precision,
@@ -47,6 +301,8 @@ __device__ __forceinline__ bool collide_adjoint(const T (&d)[9], const T (&lam)[
                                                 const CollideParams<T>& p, T (&mu)[9],
                                                 T& beta_bar)
 {
+    if constexpr (std::is_same<T, float>::value)
+        return collide_adjoint_pairs<VAR>(d, lam, p, mu, beta_bar);
     bool guarded = false;
     constexpr bool central = (VAR == kA || VAR == kB);
     const T two_beta = p.two_beta;
