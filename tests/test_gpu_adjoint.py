@@ -168,7 +168,7 @@ def test_autograd_function_returns_adjoint_gradients():
                       dtype="f64", steps=steps, ckpt_every=8, objective="misfit", u_target=tgt)
     (3.0 * J).backward()
     Jd, g, gb = _gpu_adjoint("B", "f64", 0.96, rho, ux, uy, steps, 8, 1, tx, ty)
-    assert float(J) == Jd
+    assert float(J.detach()) == Jd
     assert np.array_equal(u0.grad.cpu().numpy(), 3.0 * g)
     assert float(beta.grad) == pytest.approx(3.0 * gb, rel=1e-15)
 
